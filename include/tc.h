@@ -1,0 +1,168 @@
+/*
+ * tc.h — C ABI of libtc: cover-edge triangle counting on one GB300 (sm_103a).
+ *
+ * Method: D. A. Bader et al., "Cover Edge-Based Novel Triangle Counting"
+ * (arXiv 2403.02997).  The count follows Algorithm CETC-Seq (Section "Cover-Edge
+ * Triangle Counting"), computed in the data-parallel shape of Algorithm CETC-SM:
+ *
+ *   1. BFS levels L(v) from a root (Definition "BFS-Edge"); vertices the root does
+ *      not reach get levels from further searches started, in ascending id order,
+ *      at every still-unvisited vertex (the restart loop of Algorithm CETC-Seq);
+ *   2. the cover-edge set S = { {u, v} : L(u) == L(v) }, the horizontal edges,
+ *      which holds an edge of every triangle (Lemma "H-E", Theorem "Cover-Edge Set
+ *      Generation");
+ *   3. for each {u, v} in S with u < v, the common neighbours w of u and v are
+ *      counted when L(w) != L(u), or when L(w) == L(u) and v < w (Theorem
+ *      "Correctness": every triangle is counted exactly once).
+ *
+ * Every step runs in CUDA kernels on the device; there is no CPU path.
+ *
+ * Conventions for every call:
+ *   - vertex ids are uint32 in [0, n) and n < 2^31;
+ *   - pointers named host_* are host memory; `src`/`dst` are host or device
+ *     memory as `edges_on_device` says; everything else the library owns;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream); work is ordered on it;
+ *   - calls on one graph handle must not run concurrently from several host
+ *     threads; different handles are independent;
+ *   - a call that fails with a status other than TC_ERR_CUDA leaves the handle
+ *     valid; after TC_ERR_CUDA the CUDA context may be unusable.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_graph tc_graph; /* opaque: device CSR, level array, scratch */
+
+typedef enum tc_status {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,  /* NULL pointer, root >= n, n >= 2^31, ... */
+  TC_ERR_VERTEX_RANGE = 2, /* an edge endpoint is >= num_vertices */
+  TC_ERR_OOM = 3,          /* device allocation failed */
+  TC_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  TC_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+  TC_ERR_OVERFLOW = 6      /* sizes beyond what the library supports */
+} tc_status;
+
+/*
+ * Build a graph from an edge list (Section "Notations and Definitions": an
+ * undirected graph G = (V, E) with neighbour sets N(v)).
+ *
+ * src[i], dst[i] (i < num_edges) is one undirected edge.  Self-loops are
+ * dropped and repeated pairs (in either orientation) collapse to one edge; the
+ * stored form is a CSR with every row sorted ascending and each edge in both
+ * rows.  If edges_on_device != 0 the arrays are device pointers, else host
+ * pointers.  The arrays are copied: the caller may free them when the call
+ * returns.  Work runs on `stream`, which is synchronised before return.
+ *
+ * Errors: TC_ERR_INVALID_ARG (out == NULL, or num_edges > 0 with a NULL array,
+ * or num_vertices >= 2^31), TC_ERR_VERTEX_RANGE (an id >= num_vertices; *out
+ * stays NULL), TC_ERR_OOM, TC_ERR_CUDA.  num_vertices == 0 or num_edges == 0 is
+ * valid and gives an edgeless graph.  The handle owns all its device memory.
+ */
+tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num_edges,
+                          uint32_t num_vertices, int edges_on_device, void* stream,
+                          tc_graph** out);
+
+/* Free the handle and all device memory it owns.  NULL is accepted. */
+tc_status tc_graph_destroy(tc_graph* g);
+
+/*
+ * Sizes: n, m = number of undirected edges after canonicalising, and the
+ * largest degree d_max (Section "Notations and Definitions").  Any out pointer
+ * may be NULL.
+ */
+tc_status tc_graph_info(const tc_graph* g, uint32_t* n, uint64_t* m, uint32_t* d_max);
+
+/*
+ * Count the triangles of the graph by the cover-edge method with BFS root
+ * `root` (Algorithm CETC-Seq; any root gives the same count, the levels and
+ * the cover set depend on it).  Enqueues the whole path on `stream`, waits for
+ * it and writes the count to *count (host).
+ *
+ * Errors: TC_ERR_INVALID_ARG (root >= n while n > 0, or count == NULL),
+ * TC_ERR_TIMEOUT, TC_ERR_CUDA.  For n == 0 the count is 0.
+ */
+tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count);
+
+/*
+ * Count k graphs (roots[i] for gs[i]) in batched launches on `stream`:
+ * graphs run concurrently in shared persistent kernels over a table of
+ * per-graph device offsets.  counts (host, k entries) receives one count per
+ * graph, equal to what tc_count gives for that graph and root.  gs[i] must be
+ * pairwise distinct.  Errors as tc_count; on error no count is written.
+ */
+tc_status tc_count_many(tc_graph* const* gs, const uint32_t* roots, size_t k, void* stream,
+                        uint64_t* counts);
+
+/*
+ * Introspection of the last tc_count / tc_count_many on this handle, for
+ * parity checks.  Each call synchronises the device work of that count.
+ */
+
+/* host_levels[n] receives L(v) (int32, every vertex >= 0 after a count). */
+tc_status tc_get_levels(const tc_graph* g, int32_t* host_levels);
+
+/*
+ * The cover-edge set S (Theorem "Cover-Edge Set Generation"): *num_cover = |S|;
+ * if host_u and host_v are both non-NULL they receive the |S| pairs u < v in
+ * an unspecified order.  Pass NULL arrays to query the size first.
+ */
+tc_status tc_get_cover_edges(const tc_graph* g, uint64_t* num_cover, uint32_t* host_u,
+                             uint32_t* host_v);
+
+/* The CSR: host_row_ptr[n+1] (uint64 offsets), host_col[2m]. */
+tc_status tc_get_csr(const tc_graph* g, uint64_t* host_row_ptr, uint32_t* host_col);
+
+/* Statistics of the last count. */
+typedef struct tc_stats {
+  uint64_t triangles;   /* T */
+  uint64_t c1;          /* common neighbours on another level (Algorithm CETC-SM) */
+  uint64_t c2;          /* common neighbours on the same level; T == c1 + c2 / 3 */
+  uint64_t num_cover;   /* |S| */
+  uint64_t m;           /* undirected edges */
+  uint32_t num_levels;  /* 1 + largest level reached from the root */
+  uint32_t bfs_steps;   /* level-synchronous steps run, restarts included */
+  uint32_t bottom_up_steps;
+  uint32_t restarted;   /* 1 if vertices outside the root's component existed */
+  float ms_bfs;         /* phase times (CUDA events), ms */
+  float ms_cover;
+  float ms_intersect;
+  float ms_total;
+} tc_stats;
+
+tc_status tc_get_stats(const tc_graph* g, tc_stats* out);
+
+/* Smallest id among the vertices of largest degree (0 when n == 0). */
+tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v);
+
+/*
+ * Tunables of the count (all have defaults; see tc_params_default).  They
+ * change speed only, never results.
+ */
+typedef struct tc_params {
+  uint32_t small_max_degree; /* cover edges with both degrees <= this use the direct merge */
+  uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (power of 2) */
+  uint32_t edges_per_item;   /* cover edges per hash work item */
+  uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
+  uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
+  uint32_t reserved[3];
+} tc_params;
+
+tc_status tc_params_default(tc_params* p);
+tc_status tc_set_params(tc_graph* g, const tc_params* p);
+
+/* Human-readable name of a status. */
+const char* tc_status_string(tc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */
