@@ -1,0 +1,467 @@
+#!/usr/bin/env python3
+"""Benchmark: cover-edge triangle counting on one GB300 (per rank).
+
+Default workload: R-MAT scale 24 (2^24 vertices, edge factor 16, a=0.57
+b=0.19 c=0.19 d=0.05, ids permuted, seed 2), BFS root = the smallest id of
+largest degree.  One step = one tc_count on the device-resident CSR: BFS levels,
+restarts, cover-edge extraction, intersections and the reduction, ending with
+the count read back to the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat24|er1024|mesh4096]
+  python bench.py --impl reference ...   # the CPU oracle on bounded samples
+
+Prints one JSON line (rank 0).  value = input edges/s (undirected edges after
+canonicalising, summed over ranks, / the slowest rank's time).  With N > 1 each
+rank counts its own replica graph (seed + rank): weak scaling, no collective on
+the data path; only the timing uses a barrier and a max-reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2403_02997_gb300 import gen  # noqa: E402
+
+WORKLOADS = {"rmat24": gen.RMAT_24, "er1024": gen.ER_1024, "mesh4096": gen.MESH_4096}
+METRIC = "input edges/s (exact triangle count, tc_count on device-resident CSR)"
+L2_BYTES = 129 * 2**20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target seconds of oracle intersection work in the CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_spec(spec, rank):
+    if rank == 0:
+        return spec
+    from dataclasses import replace
+    return replace(spec, seed=spec.seed + 1000 * rank)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes of the owner-hash kernel
+# ----------------------------------------------------------------------------
+
+def hash_kernel_bytes(rp, col, cu, cv, params) -> dict:
+    """Bytes the owner-hash kernel must move, from the graph and its cover set.
+
+    Per hash-path cover edge {h, x} (h the owner, x the streamer): the part of
+    N(x) it streams (4 d(x)), its bucket entry (4) and x's row offsets (16).
+    Per work item (owner h, chunk, slice): the chunk of N(h) and those vertices'
+    levels (8 per entry) plus the owner's offsets (32).
+    """
+    deg = np.diff(rp.astype(np.int64))
+    du = deg[cu].astype(np.int64)
+    dv = deg[cv].astype(np.int64)
+    smax = params["small_max_degree"]
+    large = ~((du <= smax) & (dv <= smax))
+    u = cu[large].astype(np.int64)
+    v = cv[large].astype(np.int64)
+    du, dv = du[large], dv[large]
+    v_owns = (dv > du) | ((dv == du) & (v > u))
+    owner = np.where(v_owns, v, u)
+    d_stream = np.where(v_owns, du, dv)
+    per_edge = 4 * d_stream + 20
+    owners, oc = np.unique(owner, return_counts=True)
+    dh = deg[owners]
+    chunk, per_item = params["hash_chunk"], params["edges_per_item"]
+    slices = (oc + per_item - 1) // per_item
+    chunks = (dh + chunk - 1) // chunk
+    items = int((slices * chunks).sum())
+    per_owner = slices * (8 * dh) + 32 * slices * chunks
+    return {"bytes": int(per_edge.sum() + per_owner.sum()), "edges": int(large.sum()),
+            "items": items, "sum_stream_deg": int(d_stream.sum())}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ["count.cu", "tc_internal.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2403_02997_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the owner-hash kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"owner_hash_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ----------------------------------------------------------------------------
+
+class OracleSampler:
+    """Times the oracle (as it stands) on a bounded sample of the workload.
+
+    The graph is built by the oracle (not timed, as tc_graph_create is not in
+    the GPU step).  A sample = the oracle BFS over the whole graph + its full
+    cover-edge scan + the literal CETC-Seq intersection of every stride-th cover
+    edge; the full-graph time is estimated as bfs + scan + (sample - scan) *
+    |S| / intersected.
+    """
+
+    def __init__(self, spec, src, dst, root, target_s):
+        import oracle
+        self.o = oracle
+        self.rp, self.col = oracle.build_csr(spec.n, src, dst)
+        self.m = int(self.col.size // 2)
+        self.root = root
+        t = time.perf_counter()
+        self.lv = oracle.bfs_levels(self.rp, self.col, root)
+        self.t_bfs = time.perf_counter() - t
+        t = time.perf_counter()
+        r0 = oracle.cetc(self.rp, self.col, self.lv, stride=1 << 62)
+        self.t_scan = time.perf_counter() - t
+        self.num_cover = r0["num_cover"]
+        s1 = max(1, self.num_cover // 512)
+        t = time.perf_counter()
+        r1 = oracle.cetc(self.rp, self.col, self.lv, stride=s1)
+        t1 = time.perf_counter() - t
+        per_edge = max(t1 - self.t_scan, 1e-9) / max(r1["done"], 1)
+        self.stride = max(1, int(math.ceil(self.num_cover * per_edge / max(target_s, 0.1))))
+
+    def step(self) -> dict:
+        t = time.perf_counter()
+        lv = self.o.bfs_levels(self.rp, self.col, self.root)
+        t_bfs = time.perf_counter() - t
+        t = time.perf_counter()
+        r = self.o.cetc(self.rp, self.col, lv, stride=self.stride)
+        t_s = time.perf_counter() - t
+        est = t_bfs + self.t_scan + max(t_s - self.t_scan, 0.0) * self.num_cover / max(r["done"], 1)
+        return {"est_seconds": est, "edges": self.m, "done": r["done"], "wall": t_bfs + t_s}
+
+    def describe(self, done) -> str:
+        return (f"oracle BFS over the whole graph + full cover-edge scan + literal CETC-Seq "
+                f"intersection of 1 in {self.stride} cover edges ({done} of {self.num_cover}), "
+                f"full-graph time scaled from the sample; 1 thread")
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]
+    src, dst = spec.edges()
+    import oracle
+    rp, _ = oracle.build_csr(spec.n, src, dst)
+    root = oracle.max_degree_root(rp) if spec.root == "maxdeg" else 0
+    del rp
+    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    sam = OracleSampler(spec, src, dst, root, target_s=budget)
+    for _ in range(args.warmup):
+        sam.step()
+    tot_edges, tot_s, done = 0, 0.0, 0
+    for _ in range(args.steps):
+        r = sam.step()
+        tot_edges += r["edges"]
+        tot_s += r["est_seconds"]
+        done = r["done"]
+    value = tot_edges / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": config_dict(spec, args),
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sam.describe(done)},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(spec, args):
+    c = {"workload": args.workload, "family": spec.family, "n": spec.n, "seed": spec.seed,
+         "root": "max-degree (smallest id)" if spec.root == "maxdeg" else "vertex 0",
+         "l2": "inputs larger than L2 (CSR > 129 MB)" if args.workload != "er1024"
+               else "input fits in L2 (small config)"}
+    if spec.family == "rmat":
+        c.update(scale=spec.scale, edge_factor=spec.edge_factor, abcd=[0.57, 0.19, 0.19, 0.05],
+                 draws=spec.draws)
+    elif spec.family == "mesh":
+        c.update(rows=spec.rows, cols=spec.cols, p=spec.p)
+    else:
+        c.update(draws=spec.draws)
+    c["parallelism"] = f"replicas x{args.gpus}"
+    return c
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2403_02997_gb300 as tc
+    from paper_2403_02997_gb300 import build as tcbuild
+    tcbuild.build_all()
+    torch.cuda.set_device(local)
+    spec = replica_spec(WORKLOADS[args.workload], rank)
+    src, dst = spec.edges()
+    E = int(src.size)
+    stream = torch.cuda.Stream()
+    h_src = torch.from_numpy(src.view(np.int32)).pin_memory()
+    h_dst = torch.from_numpy(dst.view(np.int32)).pin_memory()
+    with torch.cuda.stream(stream):
+        d_src = h_src.to("cuda", non_blocking=True)
+        d_dst = h_dst.to("cuda", non_blocking=True)
+    stream.synchronize()
+    g = tc.Graph(d_src, d_dst, spec.n, stream=stream)
+    del d_src, d_dst
+    root = g.max_degree_vertex() if spec.root == "maxdeg" else 0
+    params = tc.tc_params_default()
+
+    counts = []
+    for _ in range(args.warmup):
+        counts.append(g.count(root, stream=stream))
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms_hash, ms_bfs, ms_cover, ms_inter, launches = [], [], [], [], 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        counts.append(g.count(root, stream=stream))
+        st = g.stats()
+        ms_hash.append(st["ms_hash"])
+        ms_bfs.append(st["ms_bfs"])
+        ms_cover.append(st["ms_cover"])
+        ms_inter.append(st["ms_intersect"])
+        launches += st["launches"]
+    ev1.record(stream)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    assert len(set(counts)) == 1, f"counts differ between steps: {set(counts)}"
+    st = g.stats()
+    T, m, n_cover = counts[0], g.m, st["num_cover"]
+
+    max_ms = max_over_ranks(elapsed_ms, world)
+    total_edges = sum_over_ranks(float(m) * args.steps, world)
+    value = total_edges / (max_ms / 1000.0)
+
+    # roofline of the dominant kernel (owner-hash intersection), algorithmic bytes
+    rp, col = g.csr()
+    cu, cv = g.cover_edges()
+    hb = hash_kernel_bytes(rp, col, cu, cv, params)
+    deg = np.diff(rp.astype(np.int64))
+    survey_bytes = int(24 * m + 12 * spec.n + 16 * n_cover +
+                       4 * (deg[cu].sum() + deg[cv].sum()) + 4 * (st["c1"] + st["c2"]))
+    del rp, col, cu, cv, deg
+    peak, peak_kind = measured_peaks()
+    hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
+    achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0
+    traffic = profiled_traffic(args.workload)
+
+    # end to end through the C ABI from pinned host buffers
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gh = tc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), spec.n,
+                      stream=stream)
+        r = gh.max_degree_vertex() if spec.root == "maxdeg" else 0
+        c = gh.count(r, stream=stream)
+        gh.close()
+        assert c == T
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    e2e_max = max_over_ranks(t_e2e, world)
+    e2e_value = sum_over_ranks(float(m), world) / e2e_max
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            sam = OracleSampler(spec, src, dst, root, target_s=args.cpu_seconds)
+            r = sam.step()
+            cpu = {"value": r["edges"] / r["est_seconds"], "unit": "edges/s", "cores": 1,
+                   "kind": "oracle", "sample": sam.describe(r["done"]),
+                   "est_full_seconds": r["est_seconds"]}
+        except Exception as e:  # keep the GPU line even if the host runs short
+            cpu = {"value": None, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {e}"}
+
+    if rank != 0:
+        g.close()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded counter-based generator)",
+        "config": config_dict(spec, args),
+        "triangles": T, "m": m, "num_cover": n_cover, "covering_ratio": n_cover / max(m, 1),
+        "cover_intersections_per_s": n_cover / (statistics.mean(ms_inter) / 1e3)
+        if statistics.mean(ms_inter) > 0 else None,
+        "phase_ms": {"bfs": statistics.mean(ms_bfs), "cover": statistics.mean(ms_cover),
+                     "intersect": statistics.mean(ms_inter), "owner_hash": hash_ms},
+        "bfs": {"levels": st["num_levels"], "steps": st["bfs_steps"],
+                "bottom_up_steps": st["bottom_up_steps"], "restarted": st["restarted"]},
+        "roofline": {"bound": "hbm", "kernel": "k_owner_hash", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "alg_bytes_per_launch": hb["bytes"], "hash_edges": hb["edges"],
+                     "hash_items": hb["items"], "survey_alg_bytes_per_count": survey_bytes},
+        "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 8 * E,
+                "d2h_bytes_per_step": 8, "seconds_per_step": e2e_max},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

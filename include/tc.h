@@ -135,6 +135,10 @@ typedef struct tc_stats {
   float ms_cover;
   float ms_intersect;
   float ms_total;
+  float ms_hash;        /* the owner-hash intersection kernel alone */
+  uint32_t launches;    /* kernels launched by the count */
+  uint64_t hash_items;  /* owner-hash work items */
+  uint64_t hash_edges;  /* cover edges on the owner-hash path */
 } tc_stats;
 
 tc_status tc_get_stats(const tc_graph* g, tc_stats* out);

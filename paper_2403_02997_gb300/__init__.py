@@ -1,0 +1,275 @@
+"""Cover-edge triangle counting on GB300: Python binding of libtc.
+
+Thin ctypes marshalling over the C ABI declared in ``include/tc.h``: every step
+of the count (CSR build, BFS levels, cover-edge extraction, intersections,
+reduction) runs in the library's CUDA kernels.  There is no CPU fallback: if
+``libtc.so`` is missing or no GPU is present, calls raise.
+
+Low-level functions carry the ABI names (``tc_graph_create``, ``tc_count``,
+``tc_count_many``, ...); ``Graph`` wraps a handle for convenience.  Device
+memory and streams may come from PyTorch: pass CUDA tensors as edge arrays and
+a ``torch.cuda.Stream`` (or a raw ``cudaStream_t`` as int) as ``stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OK = 0
+STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_VERTEX_RANGE", 3: "TC_ERR_OOM",
+                4: "TC_ERR_CUDA", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_OVERFLOW"}
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {name}{(' (' + detail + ')') if detail else ''}")
+
+
+class tc_stats(ctypes.Structure):
+    _fields_ = [("triangles", ctypes.c_uint64), ("c1", ctypes.c_uint64), ("c2", ctypes.c_uint64),
+                ("num_cover", ctypes.c_uint64), ("m", ctypes.c_uint64),
+                ("num_levels", ctypes.c_uint32), ("bfs_steps", ctypes.c_uint32),
+                ("bottom_up_steps", ctypes.c_uint32), ("restarted", ctypes.c_uint32),
+                ("ms_bfs", ctypes.c_float), ("ms_cover", ctypes.c_float),
+                ("ms_intersect", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ms_hash", ctypes.c_float), ("launches", ctypes.c_uint32),
+                ("hash_items", ctypes.c_uint64), ("hash_edges", ctypes.c_uint64)]
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [("small_max_degree", ctypes.c_uint32), ("hash_chunk", ctypes.c_uint32),
+                ("edges_per_item", ctypes.c_uint32), ("bfs_alpha", ctypes.c_uint32),
+                ("bfs_beta", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtc.so (built by ``paper_2403_02997_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libtc.so not found at {path}: run __graft_entry__.build() or "
+                          f"python -m paper_2403_02997_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    P = ctypes.POINTER
+    sig = {
+        "tc_graph_create": ([vp, vp, u64, u32, ctypes.c_int, vp, P(vp)], ctypes.c_int),
+        "tc_graph_destroy": ([vp], ctypes.c_int),
+        "tc_graph_info": ([vp, P(u32), P(u64), P(u32)], ctypes.c_int),
+        "tc_count": ([vp, u32, vp, P(u64)], ctypes.c_int),
+        "tc_count_many": ([P(vp), P(u32), ctypes.c_size_t, vp, P(u64)], ctypes.c_int),
+        "tc_get_levels": ([vp, vp], ctypes.c_int),
+        "tc_get_cover_edges": ([vp, P(u64), vp, vp], ctypes.c_int),
+        "tc_get_csr": ([vp, vp, vp], ctypes.c_int),
+        "tc_get_stats": ([vp, P(tc_stats)], ctypes.c_int),
+        "tc_max_degree_vertex": ([vp, P(u32)], ctypes.c_int),
+        "tc_params_default": ([P(tc_params)], ctypes.c_int),
+        "tc_set_params": ([vp, P(tc_params)], ctypes.c_int),
+        "tc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != TC_OK:
+        raise TCError(status, where)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _as_edge_array(a):
+    """(pointer, length, on_device, keepalive) for a uint32 edge array."""
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        import torch
+        if a.dtype not in (torch.int32, torch.uint32):
+            a = a.to(torch.int32)
+        a = a.contiguous()
+        return a.data_ptr(), a.numel(), True, a
+    arr = np.ascontiguousarray(a, dtype=np.uint32)
+    return arr.ctypes.data, arr.size, False, arr
+
+
+# ----------------------------------------------------------------------------
+# ABI-named functions
+# ----------------------------------------------------------------------------
+
+def tc_graph_create(src, dst, num_vertices: int, stream=None) -> int:
+    """Build a device graph from an undirected edge list; returns the handle."""
+    lib = load_library()
+    ps, ns, ds, ks = _as_edge_array(src)
+    pd, nd, dd, kd = _as_edge_array(dst)
+    if ns != nd or ds != dd:
+        raise ValueError("src and dst must have the same length and live on the same device")
+    out = ctypes.c_void_p()
+    st = lib.tc_graph_create(ps if ns else None, pd if nd else None, ns, num_vertices, int(ds),
+                             _stream_handle(stream), ctypes.byref(out))
+    del ks, kd
+    _check(st, "tc_graph_create")
+    return out.value
+
+
+def tc_graph_destroy(handle: int) -> None:
+    _check(load_library().tc_graph_destroy(handle), "tc_graph_destroy")
+
+
+def tc_count(handle: int, root: int, stream=None) -> int:
+    c = ctypes.c_uint64()
+    _check(load_library().tc_count(handle, root, _stream_handle(stream), ctypes.byref(c)),
+           "tc_count")
+    return int(c.value)
+
+
+def tc_count_many(handles: Sequence[int], roots: Sequence[int], stream=None) -> list:
+    k = len(handles)
+    if k == 0:
+        return []
+    hs = (ctypes.c_void_p * k)(*handles)
+    rs = (ctypes.c_uint32 * k)(*roots)
+    out = (ctypes.c_uint64 * k)()
+    _check(load_library().tc_count_many(hs, rs, k, _stream_handle(stream), out), "tc_count_many")
+    return [int(x) for x in out]
+
+
+def tc_graph_info(handle: int):
+    n, m, d = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load_library().tc_graph_info(handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d)),
+           "tc_graph_info")
+    return int(n.value), int(m.value), int(d.value)
+
+
+def tc_get_levels(handle: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.int32)
+    _check(load_library().tc_get_levels(handle, out.ctypes.data if n else None), "tc_get_levels")
+    return out
+
+
+def tc_get_cover_edges(handle: int):
+    lib = load_library()
+    k = ctypes.c_uint64()
+    _check(lib.tc_get_cover_edges(handle, ctypes.byref(k), None, None), "tc_get_cover_edges")
+    u = np.empty(k.value, dtype=np.uint32)
+    v = np.empty(k.value, dtype=np.uint32)
+    if k.value:
+        _check(lib.tc_get_cover_edges(handle, ctypes.byref(k), u.ctypes.data, v.ctypes.data),
+               "tc_get_cover_edges")
+    return u, v
+
+
+def tc_get_csr(handle: int, n: int, m: int):
+    rp = np.empty(n + 1, dtype=np.uint64)
+    col = np.empty(2 * m, dtype=np.uint32)
+    _check(load_library().tc_get_csr(handle, rp.ctypes.data, col.ctypes.data if m else None),
+           "tc_get_csr")
+    return rp, col
+
+
+def tc_get_stats(handle: int) -> dict:
+    s = tc_stats()
+    _check(load_library().tc_get_stats(handle, ctypes.byref(s)), "tc_get_stats")
+    return {name: getattr(s, name) for name, _ in tc_stats._fields_}
+
+
+def tc_max_degree_vertex(handle: int) -> int:
+    v = ctypes.c_uint32()
+    _check(load_library().tc_max_degree_vertex(handle, ctypes.byref(v)), "tc_max_degree_vertex")
+    return int(v.value)
+
+
+def tc_params_default() -> dict:
+    p = tc_params()
+    _check(load_library().tc_params_default(ctypes.byref(p)), "tc_params_default")
+    return {name: getattr(p, name) for name, _ in tc_params._fields_ if name != "reserved"}
+
+
+def tc_set_params(handle: int, **kw) -> None:
+    p = tc_params()
+    lib = load_library()
+    _check(lib.tc_params_default(ctypes.byref(p)), "tc_params_default")
+    for k, v in kw.items():
+        setattr(p, k, int(v))
+    _check(lib.tc_set_params(handle, ctypes.byref(p)), "tc_set_params")
+
+
+# ----------------------------------------------------------------------------
+# Convenience wrapper
+# ----------------------------------------------------------------------------
+
+class Graph:
+    """A device-resident graph (owns one tc_graph handle)."""
+
+    def __init__(self, src, dst, num_vertices: int, stream=None):
+        self.handle = tc_graph_create(src, dst, num_vertices, stream)
+        self.n, self.m, self.d_max = tc_graph_info(self.handle)
+
+    def count(self, root: Optional[int] = None, stream=None) -> int:
+        if root is None:
+            root = 0
+        return tc_count(self.handle, root, stream)
+
+    def max_degree_vertex(self) -> int:
+        return tc_max_degree_vertex(self.handle)
+
+    def levels(self) -> np.ndarray:
+        return tc_get_levels(self.handle, self.n)
+
+    def cover_edges(self):
+        return tc_get_cover_edges(self.handle)
+
+    def csr(self):
+        return tc_get_csr(self.handle, self.n, self.m)
+
+    def stats(self) -> dict:
+        return tc_get_stats(self.handle)
+
+    def set_params(self, **kw) -> None:
+        tc_set_params(self.handle, **kw)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            tc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def count_many(graphs: Sequence[Graph], roots: Sequence[int], stream=None) -> list:
+    return tc_count_many([g.handle for g in graphs], roots, stream)

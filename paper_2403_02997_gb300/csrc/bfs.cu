@@ -1,0 +1,325 @@
+// BFS levels (Definition "BFS-Edge": L(v) = shortest distance from the root)
+// with the restart rule of Algorithm CETC-Seq (a new search from every vertex
+// still unvisited, taken in ascending id order), computed level-synchronously.
+//
+// Root phase: level-synchronous, direction-optimising (Beamer et al.):
+//   top-down  k_bfs_td    frontier queue; edges of the frontier are spread
+//                         evenly over the grid through a scan of frontier
+//                         degrees, so a hub row uses every SM; a vertex is
+//                         claimed with atomicCAS(level, -1, l+1);
+//   bottom-up k_bfs_bu    every unvisited vertex scans its row (8 lanes per
+//                         vertex, early exit) for a neighbour at level l.
+//   Switch to bottom-up when the frontier's edges exceed the unexplored edges
+//   / alpha; back to top-down when the frontier falls below n / beta.
+// Restart phase: the vertices left unvisited form whole components.  Their
+//   components are found by union-find that always hooks the larger root under
+//   the smaller, so each root is its component's smallest id — exactly the
+//   vertex the ascending restart loop starts from.  One multi-source BFS from
+//   all those roots (level 0) then gives every level at once; components do not
+//   interact, so the levels equal those of the sequential restarts.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kTdBlock = 256;
+constexpr int kTdEdgesPerBlock = 2048;
+constexpr int kBuBlock = 256;
+constexpr int kBuGroup = 8;
+
+__global__ void k_set_root(int32_t* level, uint32_t* queue, uint32_t root) {
+  level[root] = 0;
+  queue[0] = root;
+}
+
+__global__ void k_frontier_degrees(const uint32_t* __restrict__ queue, uint64_t qlen,
+                                   const unsigned long long* __restrict__ row_ptr,
+                                   uint32_t* __restrict__ fdeg) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < qlen;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t u = queue[i];
+    fdeg[i] = (uint32_t)(row_ptr[u + 1] - row_ptr[u]);
+  }
+}
+
+// Largest i in [lo, hi] with qoff[i] <= e (qoff nondecreasing, qoff[lo] <= e).
+__device__ __forceinline__ uint64_t frontier_index(const unsigned long long* qoff, uint64_t lo,
+                                                   uint64_t hi, unsigned long long e) {
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo + 1) / 2;
+    if (qoff[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void warp_append(bool take, uint32_t value, uint32_t* queue,
+                                            unsigned long long* len) {
+  const unsigned mask = __ballot_sync(0xffffffffu, take);
+  if (!mask) return;
+  const unsigned lane = lane_id();
+  unsigned long long base = 0;
+  const unsigned leader = __ffs(mask) - 1;
+  if (lane == leader) base = atomicAdd(len, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (take) queue[base + __popc(mask & ((1u << lane) - 1u))] = value;
+}
+
+__global__ void __launch_bounds__(kTdBlock) k_bfs_td(const unsigned long long* __restrict__ row_ptr,
+                                                     const uint32_t* __restrict__ col,
+                                                     int32_t* __restrict__ level,
+                                                     const uint32_t* __restrict__ queue,
+                                                     uint64_t qlen,
+                                                     const unsigned long long* __restrict__ qoff,
+                                                     int32_t next_level,
+                                                     uint32_t* __restrict__ next_queue,
+                                                     DevCounters* ctr) {
+  __shared__ uint64_t s_lo, s_hi;
+  const unsigned long long total = qoff[qlen];
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * kTdEdgesPerBlock; e0 < total;
+       e0 += (unsigned long long)gridDim.x * kTdEdgesPerBlock) {
+    const unsigned long long e1 = min(total, e0 + kTdEdgesPerBlock);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_lo = frontier_index(qoff, 0, qlen - 1, e0);
+      s_hi = frontier_index(qoff, s_lo, qlen - 1, e1 - 1);
+    }
+    __syncthreads();
+    const uint64_t lo = s_lo, hi = s_hi;
+    for (unsigned long long b = e0; b < e1; b += kTdBlock) {
+      const unsigned long long e = b + threadIdx.x;
+      bool take = false;
+      uint32_t w = 0;
+      if (e < e1) {
+        const uint64_t i = frontier_index(qoff, lo, hi, e);
+        const uint32_t u = queue[i];
+        w = col[row_ptr[u] + (e - qoff[i])];
+        if (level[w] == -1) take = atomicCAS(&level[w], -1, next_level) == -1;
+      }
+      warp_append(take, w, next_queue, &ctr->next_n);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBuBlock) k_bfs_bu(const unsigned long long* __restrict__ row_ptr,
+                                                     const uint32_t* __restrict__ col,
+                                                     int32_t* __restrict__ level, uint32_t n,
+                                                     int32_t cur_level, DevCounters* ctr) {
+  const unsigned lane = lane_id();
+  const unsigned sub = lane & (kBuGroup - 1);
+  const unsigned gmask = 0xFFu << (lane & ~(kBuGroup - 1u));
+  const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / kBuGroup;
+  unsigned long long found = 0;
+  for (uint64_t v = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / kBuGroup; v < n;
+       v += groups) {
+    if (level[v] != -1) continue;
+    const unsigned long long b = row_ptr[v], e = row_ptr[v + 1];
+    bool hit_any = false;
+    for (unsigned long long j0 = b; j0 < e; j0 += kBuGroup) {
+      const unsigned long long j = j0 + sub;
+      const bool hit = j < e && level[col[j]] == cur_level;
+      if (__ballot_sync(gmask, hit) & gmask) {
+        hit_any = true;
+        break;
+      }
+    }
+    if (hit_any && sub == 0) {
+      level[v] = cur_level + 1;
+      ++found;
+    }
+  }
+  found = warp_sum(found);
+  if (lane == 0 && found) atomicAdd(&ctr->next_n, found);
+}
+
+__global__ void k_collect_level(const int32_t* __restrict__ level, uint32_t n, int32_t want,
+                                uint32_t* __restrict__ queue, DevCounters* ctr) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t iters = ((uint64_t)n + stride - 1) / stride;
+  for (uint64_t it = 0; it < iters; ++it) {
+    const uint64_t v = it * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool take = v < n && level[v] == want;
+    warp_append(take, (uint32_t)v, queue, &ctr->next_n);
+  }
+}
+
+__global__ void k_count_unvisited(const int32_t* __restrict__ level, uint32_t n, DevCounters* ctr) {
+  unsigned long long c = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    c += level[v] == -1;
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) atomicAdd(&ctr->unvisited, c);
+}
+
+// ---- restart components -------------------------------------------------
+
+__global__ void k_cc_init(uint32_t* parent, uint32_t n) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    parent[v] = (uint32_t)v;
+}
+
+__device__ __forceinline__ uint32_t cc_find(uint32_t* parent, uint32_t x) {
+  uint32_t p = parent[x];
+  while (p != x) {
+    uint32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;  // path halving; any ancestor is a valid parent
+    x = p;
+    p = gp;
+  }
+  return x;
+}
+
+// Union of the endpoints of every edge {v, w}, w < v, of an unvisited vertex v
+// (all its neighbours are unvisited too).  The larger root is hooked under the
+// smaller one with a CAS, so a root is always the minimum of its tree.
+__global__ void k_cc_hook(const unsigned long long* __restrict__ row_ptr,
+                          const uint32_t* __restrict__ col, const int32_t* __restrict__ level,
+                          uint32_t* parent, uint32_t n) {
+  const uint64_t warps = (uint64_t)gridDim.x * blockDim.x / 32;
+  for (uint64_t v = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+    if (level[v] != -1) continue;
+    const unsigned long long b = row_ptr[v], e = row_ptr[v + 1];
+    for (unsigned long long j = b + lane_id(); j < e; j += 32) {
+      uint32_t w = col[j];
+      if (w >= v) break;  // rows are sorted
+      uint32_t a = (uint32_t)v, c = w;
+      for (;;) {
+        a = cc_find(parent, a);
+        c = cc_find(parent, c);
+        if (a == c) break;
+        uint32_t hi = a > c ? a : c, lo = a > c ? c : a;
+        if (atomicCAS(&parent[hi], hi, lo) == hi) break;
+      }
+    }
+  }
+}
+
+// Roots (parent[v] == v after hooking) of unvisited vertices start the
+// restart search at level 0.
+__global__ void k_cc_seed(const uint32_t* __restrict__ parent, int32_t* __restrict__ level,
+                          uint32_t n, uint32_t* __restrict__ queue, DevCounters* ctr) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t iters = ((uint64_t)n + stride - 1) / stride;
+  for (uint64_t it = 0; it < iters; ++it) {
+    const uint64_t v = it * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    if (v < n && level[v] == -1 && parent[v] == (uint32_t)v) {
+      level[v] = 0;
+      take = true;
+    }
+    warp_append(take, (uint32_t)v, queue, &ctr->next_n);
+  }
+}
+
+tc_status read_counters(tc_graph* g, cudaStream_t st) {
+  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  return TC_OK;
+}
+
+tc_status reset_next(tc_graph* g, cudaStream_t st) {
+  TC_CUDA_TRY(cudaMemsetAsync(&g->ctr->next_n, 0, sizeof(unsigned long long), st));
+  return TC_OK;
+}
+
+// Level-synchronous search from the vertices already in queue_a (qlen of them,
+// all at level 0).  Returns the number of levels (1 + deepest level).
+tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* levels_out) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  uint32_t* q = g->queue_a;
+  uint32_t* nq = g->queue_b;
+  bool bottom_up = false;
+  long double unexplored = (long double)g->nnz;
+  int32_t lvl = 0;
+  const uint32_t alpha = g->params.bfs_alpha ? g->params.bfs_alpha : 15;
+  const uint32_t beta = g->params.bfs_beta ? g->params.bfs_beta : 18;
+  uint64_t prev_frontier = qlen;
+  while (true) {
+    unsigned long long fedges = 0;
+    if (!bottom_up) {
+      if (qlen == 0) break;
+      k_frontier_degrees<<<grid_for(qlen, 256, sms * 16), 256, 0, st>>>(q, qlen, g->row_ptr, g->fdeg); TC_LAUNCHED();
+      TC_CUDA_TRY(cudaGetLastError());
+      TC_TRY(exclusive_scan_u32(g->fdeg, g->qoff, qlen, g->scan, st));
+      TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr_host->scan_total, g->qoff + qlen, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st));
+      TC_CUDA_TRY(cudaStreamSynchronize(st));
+      fedges = g->ctr_host->scan_total;
+      if ((long double)fedges * alpha > unexplored && qlen > 1) bottom_up = true;
+    }
+    TC_TRY(reset_next(g, st));
+    uint64_t found;
+    if (!bottom_up) {
+      if (fedges > 0) {
+        k_bfs_td<<<grid_for(fedges, kTdEdgesPerBlock, sms * 8), kTdBlock, 0, st>>>(
+            g->row_ptr, g->col, g->level, q, qlen, g->qoff, lvl + 1, nq, g->ctr); TC_LAUNCHED();
+        TC_CUDA_TRY(cudaGetLastError());
+      }
+      TC_TRY(read_counters(g, st));
+      found = g->ctr_host->next_n;
+      uint32_t* t = q;
+      q = nq;
+      nq = t;
+      qlen = found;
+    } else {
+      k_bfs_bu<<<sms * 8, kBuBlock, 0, st>>>(g->row_ptr, g->col, g->level, n, lvl, g->ctr); TC_LAUNCHED();
+      TC_CUDA_TRY(cudaGetLastError());
+      TC_TRY(read_counters(g, st));
+      found = g->ctr_host->next_n;
+      g->stats.bottom_up_steps++;
+      if (found > 0 && found < n / beta && found < prev_frontier) {
+        TC_TRY(reset_next(g, st));
+        k_collect_level<<<sms * 8, 256, 0, st>>>(g->level, n, lvl + 1, q, g->ctr); TC_LAUNCHED();
+        TC_CUDA_TRY(cudaGetLastError());
+        TC_TRY(read_counters(g, st));
+        qlen = g->ctr_host->next_n;
+        bottom_up = false;
+      }
+    }
+    g->stats.bfs_steps++;
+    unexplored -= (long double)fedges;
+    prev_frontier = found;
+    if (found == 0) break;
+    ++lvl;
+  }
+  *levels_out = (uint32_t)lvl + 1;
+  return TC_OK;
+}
+
+}  // namespace
+
+tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  g->stats.bfs_steps = 0;
+  g->stats.bottom_up_steps = 0;
+  g->stats.restarted = 0;
+  TC_CUDA_TRY(cudaMemsetAsync(g->level, 0xFF, sizeof(int32_t) * n, st));
+  k_set_root<<<1, 1, 0, st>>>(g->level, g->queue_a, root); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  uint32_t levels = 0;
+  TC_TRY(level_loop(g, 1, st, &levels));
+  g->stats.num_levels = levels;
+
+  // restart phase
+  TC_CUDA_TRY(cudaMemsetAsync(&g->ctr->unvisited, 0, sizeof(unsigned long long), st));
+  k_count_unvisited<<<sms * 8, 256, 0, st>>>(g->level, n, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  TC_TRY(read_counters(g, st));
+  if (g->ctr_host->unvisited == 0) return TC_OK;
+  g->stats.restarted = 1;
+  k_cc_init<<<sms * 8, 256, 0, st>>>(g->parent, n); TC_LAUNCHED();
+  k_cc_hook<<<sms * 16, 256, 0, st>>>(g->row_ptr, g->col, g->level, g->parent, n); TC_LAUNCHED();
+  TC_TRY(reset_next(g, st));
+  k_cc_seed<<<sms * 8, 256, 0, st>>>(g->parent, g->level, n, g->queue_a, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  TC_TRY(read_counters(g, st));
+  uint32_t more = 0;
+  TC_TRY(level_loop(g, g->ctr_host->next_n, st, &more));
+  return TC_OK;
+}
+
+}  // namespace tc

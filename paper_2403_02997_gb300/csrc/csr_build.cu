@@ -1,0 +1,307 @@
+// Graph construction on the device: canonical undirected simple graph -> CSR
+// with rows sorted ascending (the input form of every routine in the paper's
+// evaluation framework, Section "Open Source Evaluation Framework"; the graph is
+// undirected and simple per Section "Notations and Definitions").
+//
+//   1. k_make_keys     each pair (u, v), u != v, becomes the two keys
+//                      (u << kb) | v and (v << kb) | u; self-loops become the
+//                      all-ones sentinel, which sorts last;
+//   2. LSD radix sort  8-bit digits over the 2*kb key bits: per pass a tile
+//                      histogram, a scan of the digit-major histogram table and
+//                      a stable scatter (warp match + per-warp digit counts);
+//   3. k_dedup_*       drop repeats (a key equal to its predecessor) with a
+//                      reduce-then-scan, write col[] and fill row_ptr[] at row
+//                      starts, so empty rows get the offset of the next row.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr unsigned long long kSentinel = ~0ull;
+
+__global__ void k_make_keys(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                            uint64_t E, uint32_t n, int kb, ulonglong2* __restrict__ keys,
+                            DevCounters* ctr) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
+    uint32_t u = src[i], v = dst[i];
+    ulonglong2 k;
+    if (u >= n || v >= n) {
+      atomicOr(&ctr->err, kErrVertexRange);
+      k.x = k.y = kSentinel;
+    } else if (u == v) {
+      k.x = k.y = kSentinel;
+    } else {
+      k.x = ((unsigned long long)u << kb) | v;
+      k.y = ((unsigned long long)v << kb) | u;
+    }
+    keys[i] = k;
+  }
+}
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortBlock = 256;  // == kRadix: one digit owner per thread
+constexpr int kSortItems = 32;
+constexpr uint64_t kSortTile = (uint64_t)kSortBlock * kSortItems;
+constexpr int kSortWarps = kSortBlock / 32;
+static_assert(kSortBlock == kRadix, "digit ownership assumes one thread per digit");
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_hist(const unsigned long long* __restrict__ keys,
+                                                           uint64_t N, int shift, uint32_t nb,
+                                                           uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[kRadix];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+#pragma unroll 8
+  for (int k = 0; k < kSortItems; ++k) {
+    uint64_t i = base + (uint64_t)k * kSortBlock + threadIdx.x;
+    if (i < N) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter.  Keys are taken in rounds of kSortBlock (round r, thread t
+// holds key r*kSortBlock + t: index order) and ranked within a round by
+// (warp, lane), so equal digits keep their input order.  Thread d owns digit d:
+// it turns the per-warp counts of the round into absolute output positions and
+// advances the digit's running offset.
+__global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned long long* __restrict__ in,
+                                                              unsigned long long* __restrict__ out,
+                                                              uint64_t N, int shift, uint32_t nb,
+                                                              const unsigned long long* __restrict__ offs) {
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ unsigned long long pos[kSortWarps][kRadix];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, dd = threadIdx.x;
+  unsigned long long run_off = offs[(uint64_t)dd * nb + blockIdx.x];
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wcnt[w][dd] = 0;
+  __syncthreads();
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const uint64_t i = base + (uint64_t)r * kSortBlock + threadIdx.x;
+    const bool valid = i < N;
+    const unsigned long long key = valid ? in[i] : 0ull;
+    const unsigned d = valid ? ((unsigned)(key >> shift) & (kRadix - 1)) : (unsigned)kRadix;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned lower = __popc(peers & lt_mask);
+    if (valid && lower == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      unsigned c = wcnt[w][dd];
+      wcnt[w][dd] = 0;
+      pos[w][dd] = run_off;
+      run_off += c;
+    }
+    __syncthreads();
+    if (valid) out[pos[warp][d] + lower] = key;
+  }
+}
+
+constexpr int kDedupBlock = 512;
+constexpr int kDedupItems = 8;
+constexpr uint64_t kDedupTile = (uint64_t)kDedupBlock * kDedupItems;
+
+__device__ __forceinline__ bool is_kept(const unsigned long long* keys, uint64_t i,
+                                        unsigned long long k) {
+  return k != kSentinel && (i == 0 || keys[i - 1] != k);
+}
+
+__global__ void __launch_bounds__(kDedupBlock) k_dedup_reduce(const unsigned long long* __restrict__ keys,
+                                                              uint64_t N,
+                                                              unsigned long long* __restrict__ sums) {
+  __shared__ unsigned long long tmp[kDedupBlock / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kDedupTile;
+  unsigned long long c = 0;
+#pragma unroll
+  for (int k = 0; k < kDedupItems; ++k) {
+    uint64_t i = base + (uint64_t)k * kDedupBlock + threadIdx.x;
+    if (i < N && is_kept(keys, i, keys[i])) ++c;
+  }
+  c = block_sum(c, tmp);
+  if (threadIdx.x == 0) sums[blockIdx.x] = c;
+}
+
+// Writes col[] and row_ptr[].  A kept key that starts row u sets row_ptr[x] for
+// every x in (previous key's row, u]; the last non-sentinel key (kept or a
+// repeat) sets row_ptr[x] = nnz for x in (its row, n].
+__global__ void __launch_bounds__(kDedupBlock) k_dedup_write(const unsigned long long* __restrict__ keys,
+                                                             uint64_t N, int kb, uint32_t n,
+                                                             const unsigned long long* __restrict__ offs,
+                                                             const unsigned long long* __restrict__ nnz_ptr,
+                                                             uint32_t* __restrict__ col,
+                                                             unsigned long long* __restrict__ row_ptr) {
+  __shared__ unsigned long long tmp[kDedupBlock / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kDedupTile + (uint64_t)threadIdx.x * kDedupItems;
+  const unsigned long long vmask = (1ull << kb) - 1ull;
+  unsigned long long kv[kDedupItems];
+  unsigned flags = 0;
+  unsigned long long c = 0;
+#pragma unroll
+  for (int k = 0; k < kDedupItems; ++k) {
+    uint64_t i = base + k;
+    kv[k] = i < N ? keys[i] : kSentinel;
+    if (i < N && is_kept(keys, i, kv[k])) {
+      flags |= 1u << k;
+      ++c;
+    }
+  }
+  unsigned long long total;
+  unsigned long long p = block_exclusive_scan(c, tmp, &total) + offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kDedupItems; ++k) {
+    const uint64_t i = base + k;
+    const unsigned long long key = kv[k];
+    if (key == kSentinel) continue;
+    const long long u = (long long)(key >> kb);
+    if (flags & (1u << k)) {
+      col[p] = (uint32_t)(key & vmask);
+      const long long prev_u = (i == 0) ? -1ll : (long long)(keys[i - 1] >> kb);
+      if (prev_u < u)
+        for (long long x = prev_u + 1; x <= u; ++x) row_ptr[x] = p;
+      ++p;
+    }
+    if (i + 1 == N || keys[i + 1] == kSentinel) {
+      const unsigned long long nnz = *nnz_ptr;
+      for (long long x = u + 1; x <= (long long)n; ++x) row_ptr[x] = nnz;
+    }
+  }
+}
+
+__global__ void k_degree_stats(const unsigned long long* __restrict__ row_ptr, uint32_t n,
+                               unsigned int* dmax) {
+  unsigned best = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    best = max(best, (unsigned)(row_ptr[v + 1] - row_ptr[v]));
+  best = __reduce_max_sync(0xffffffffu, best);
+  if (lane_id() == 0) atomicMax(dmax, best);
+}
+
+__global__ void k_maxdeg_vertex(const unsigned long long* __restrict__ row_ptr, uint32_t n,
+                                const unsigned int* dmax, unsigned int* vmin) {
+  const unsigned target = *dmax;
+  unsigned best = 0xFFFFFFFFu;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    if ((unsigned)(row_ptr[v + 1] - row_ptr[v]) == target) best = min(best, (unsigned)v);
+  best = __reduce_min_sync(0xffffffffu, best);
+  if (lane_id() == 0 && best != 0xFFFFFFFFu) atomicMin(vmin, best);
+}
+
+int key_bits(uint32_t n) {
+  if (n <= 2) return 1;
+  uint32_t x = n - 1;
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+}  // namespace
+
+tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
+                    cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int kb = key_bits(n);
+  const uint64_t N = 2 * E;
+  unsigned long long* keys_a = nullptr;
+  unsigned long long* keys_b = nullptr;
+  uint32_t* hist = nullptr;
+  unsigned long long* hoff = nullptr;
+  tc_status status = TC_OK;
+  auto fail = [&](tc_status s) {
+    status = s;
+    return s;
+  };
+
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  g->row_ptr = nullptr;
+  TC_CUDA_TRY(cudaMalloc(&g->row_ptr, sizeof(unsigned long long) * ((size_t)n + 1)));
+  if (N == 0) {
+    TC_CUDA_TRY(cudaMemsetAsync(g->row_ptr, 0, sizeof(unsigned long long) * ((size_t)n + 1), st));
+    g->nnz = 0;
+    g->m = 0;
+  } else {
+    const uint64_t nb = (N + kSortTile - 1) / kSortTile;
+    const uint64_t ndb = (N + kDedupTile - 1) / kDedupTile;
+    if (nb > 0x7FFFFFFFull) return TC_ERR_OVERFLOW;
+    do {
+      if (cudaMalloc(&keys_a, sizeof(unsigned long long) * N) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (cudaMalloc(&keys_b, sizeof(unsigned long long) * N) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (cudaMalloc(&hist, sizeof(uint32_t) * kRadix * nb) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      const uint64_t hcount = (uint64_t)kRadix * nb;
+      const uint64_t off_entries = (hcount > ndb ? hcount : ndb) + 1;
+      if (cudaMalloc(&hoff, sizeof(unsigned long long) * off_entries) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      ScanScratch ss;
+      ss.capacity = scan_scratch_entries(off_entries);
+      if (cudaMalloc(&ss.sums, sizeof(unsigned long long) * ss.capacity) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+
+      k_make_keys<<<grid_for(E, 256, 152 * 64), 256, 0, st>>>(d_src, d_dst, E, n, kb,
+                                                             reinterpret_cast<ulonglong2*>(keys_a),
+                                                             g->ctr); TC_LAUNCHED();
+      for (int shift = 0; shift < 2 * kb && status == TC_OK; shift += kRadixBits) {
+        k_radix_hist<<<(unsigned)nb, kSortBlock, 0, st>>>(keys_a, N, shift, (uint32_t)nb, hist); TC_LAUNCHED();
+        if (exclusive_scan_u32(hist, hoff, hcount, ss, st) != TC_OK) { fail(TC_ERR_CUDA); break; }
+        k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, st>>>(keys_a, keys_b, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
+        unsigned long long* t = keys_a;
+        keys_a = keys_b;
+        keys_b = t;
+      }
+      if (status != TC_OK) { cudaFree(ss.sums); break; }
+      k_dedup_reduce<<<(unsigned)ndb, kDedupBlock, 0, st>>>(keys_a, N, hoff); TC_LAUNCHED();
+      if (exclusive_scan_u64(hoff, hoff, ndb, ss, st) != TC_OK) { cudaFree(ss.sums); fail(TC_ERR_CUDA); break; }
+      unsigned long long nnz = 0;
+      unsigned int err = 0;
+      cudaMemcpyAsync(&nnz, hoff + ndb, sizeof(nnz), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&err, &g->ctr->err, sizeof(err), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(ss.sums); fail(TC_ERR_CUDA); break; }
+      cudaFree(ss.sums);
+      if (err & kErrVertexRange) { fail(TC_ERR_VERTEX_RANGE); break; }
+      g->nnz = nnz;
+      g->m = nnz / 2;
+      if (nnz == 0) {
+        cudaMemsetAsync(g->row_ptr, 0, sizeof(unsigned long long) * ((size_t)n + 1), st);
+        break;
+      }
+      if (cudaMalloc(&g->col, sizeof(uint32_t) * nnz) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      k_dedup_write<<<(unsigned)ndb, kDedupBlock, 0, st>>>(keys_a, N, kb, n, hoff, hoff + ndb, g->col,
+                                                           g->row_ptr); TC_LAUNCHED();
+    } while (0);
+    cudaError_t e = cudaGetLastError();
+    if (status == TC_OK && e != cudaSuccess) {
+      set_last_cuda_error(e);
+      status = TC_ERR_CUDA;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(keys_a);
+    cudaFree(keys_b);
+    cudaFree(hist);
+    cudaFree(hoff);
+    if (status != TC_OK) return status;
+  }
+  // degree statistics: largest degree and the smallest vertex id that has it
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  TC_CUDA_TRY(cudaMemsetAsync(&g->ctr->dmax_vertex, 0xFF, sizeof(unsigned int), st));
+  if (n > 0) {
+    k_degree_stats<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g->row_ptr, n, &g->ctr->dmax); TC_LAUNCHED();
+    k_maxdeg_vertex<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(g->row_ptr, n, &g->ctr->dmax,
+                                                               &g->ctr->dmax_vertex); TC_LAUNCHED();
+    TC_CUDA_TRY(cudaGetLastError());
+  }
+  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  g->d_max = g->ctr_host->dmax;
+  g->maxdeg_vertex = (n == 0 || g->ctr_host->dmax_vertex == 0xFFFFFFFFu) ? 0 : g->ctr_host->dmax_vertex;
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  return TC_OK;
+}
+
+}  // namespace tc

@@ -1,0 +1,308 @@
+// C ABI of libtc (declared in include/tc.h).  Argument checks, ownership of
+// device memory, and the order of the phases; the arithmetic is in the kernels
+// of csr_build.cu, bfs.cu and count.cu.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+thread_local uint32_t g_launches = 0;
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 1;
+  }
+  return cached;
+}
+
+namespace {
+
+template <typename T>
+tc_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    cudaGetLastError();
+    return TC_ERR_OOM;
+  }
+  return TC_OK;
+}
+
+void free_graph(tc_graph* g) {
+  if (!g) return;
+  void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
+                  g->ooff,    g->ioff,  g->parent, g->fdeg,    g->ocount,  g->ofill,
+                  g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (g->ctr_host) cudaFreeHost(g->ctr_host);
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
+  delete g;
+}
+
+tc_status alloc_count_state(tc_graph* g) {
+  const size_t n = g->n, m = g->m;
+  TC_TRY(dalloc(&g->level, n));
+  TC_TRY(dalloc(&g->queue_a, n));
+  TC_TRY(dalloc(&g->queue_b, n));
+  TC_TRY(dalloc(&g->qoff, n + 1));
+  TC_TRY(dalloc(&g->ooff, n + 1));
+  TC_TRY(dalloc(&g->ioff, n + 1));
+  TC_TRY(dalloc(&g->parent, n));
+  TC_TRY(dalloc(&g->fdeg, n));
+  TC_TRY(dalloc(&g->ocount, n));
+  TC_TRY(dalloc(&g->ofill, n));
+  TC_TRY(dalloc(&g->cover, m));
+  TC_TRY(dalloc(&g->large, m));
+  TC_TRY(dalloc(&g->ostream, m));
+  g->scan.capacity = scan_scratch_entries(n + 1);
+  TC_TRY(dalloc(&g->scan.sums, g->scan.capacity));
+  return TC_OK;
+}
+
+void params_default(tc_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->small_max_degree = 32;
+  p->hash_chunk = 8192;
+  p->edges_per_item = 512;
+  p->bfs_alpha = 15;
+  p->bfs_beta = 18;
+}
+
+tc_status sync_status(tc_graph* g, cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    return TC_ERR_CUDA;
+  }
+  (void)g;
+  return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+tc_status tc_params_default(tc_params* p) {
+  if (!p) return TC_ERR_INVALID_ARG;
+  params_default(p);
+  return TC_OK;
+}
+
+tc_status tc_set_params(tc_graph* g, const tc_params* p) {
+  if (!g || !p) return TC_ERR_INVALID_ARG;
+  const uint32_t c = p->hash_chunk;
+  if (c < 32 || c > 16384 || (c & (c - 1)) != 0) return TC_ERR_INVALID_ARG;
+  if (p->edges_per_item == 0 || p->bfs_alpha == 0 || p->bfs_beta == 0) return TC_ERR_INVALID_ARG;
+  g->params = *p;
+  return TC_OK;
+}
+
+tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num_edges,
+                          uint32_t num_vertices, int edges_on_device, void* stream,
+                          tc_graph** out) {
+  if (!out) return TC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (num_edges > 0 && (!src || !dst)) return TC_ERR_INVALID_ARG;
+  if (num_vertices >= 0x80000000u) return TC_ERR_INVALID_ARG;
+  if (num_edges > (1ull << 34)) return TC_ERR_OVERFLOW;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tc_graph* g = new (std::nothrow) tc_graph();
+  if (!g) return TC_ERR_OOM;
+  params_default(&g->params);
+  std::memset(&g->stats, 0, sizeof(g->stats));
+  g->n = num_vertices;
+  tc_status s = TC_OK;
+  uint32_t* staged_src = nullptr;
+  uint32_t* staged_dst = nullptr;
+  do {
+    if ((s = dalloc(&g->ctr, 1)) != TC_OK) break;
+    if (cudaMallocHost(reinterpret_cast<void**>(&g->ctr_host), sizeof(DevCounters)) != cudaSuccess) {
+      s = TC_ERR_OOM;
+      break;
+    }
+    std::memset(g->ctr_host, 0, sizeof(DevCounters));
+    bool ev_ok = true;
+    for (cudaEvent_t& e : g->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ev_ok) { s = TC_ERR_CUDA; break; }
+    const uint32_t* d_src = src;
+    const uint32_t* d_dst = dst;
+    if (num_edges > 0 && !edges_on_device) {
+      if ((s = dalloc(&staged_src, num_edges)) != TC_OK) break;
+      if ((s = dalloc(&staged_dst, num_edges)) != TC_OK) break;
+      if (cudaMemcpyAsync(staged_src, src, sizeof(uint32_t) * num_edges, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(staged_dst, dst, sizeof(uint32_t) * num_edges, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        s = TC_ERR_CUDA;
+        break;
+      }
+      d_src = staged_src;
+      d_dst = staged_dst;
+    }
+    if ((s = build_csr(g, d_src, d_dst, num_edges, st)) != TC_OK) break;
+    if ((s = alloc_count_state(g)) != TC_OK) break;
+    s = sync_status(g, st);
+  } while (0);
+  if (staged_src || staged_dst) {
+    cudaStreamSynchronize(st);
+    if (staged_src) cudaFree(staged_src);
+    if (staged_dst) cudaFree(staged_dst);
+  }
+  if (s != TC_OK) {
+    free_graph(g);
+    return s;
+  }
+  *out = g;
+  return TC_OK;
+}
+
+tc_status tc_graph_destroy(tc_graph* g) {
+  if (!g) return TC_OK;
+  cudaDeviceSynchronize();
+  free_graph(g);
+  return TC_OK;
+}
+
+tc_status tc_graph_info(const tc_graph* g, uint32_t* n, uint64_t* m, uint32_t* d_max) {
+  if (!g) return TC_ERR_INVALID_ARG;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (d_max) *d_max = g->d_max;
+  return TC_OK;
+}
+
+tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v) {
+  if (!g || !v) return TC_ERR_INVALID_ARG;
+  *v = g->maxdeg_vertex;
+  return TC_OK;
+}
+
+tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
+  if (!g || !count) return TC_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::memset(&g->stats, 0, sizeof(g->stats));
+  g->stats.m = g->m;
+  g->counted = false;
+  if (g->n == 0) {
+    *count = 0;
+    g->counted = true;
+    return TC_OK;
+  }
+  if (root >= g->n) return TC_ERR_INVALID_ARG;
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_TRY(run_bfs(g, root, st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  TC_TRY(run_cover_and_count(g, st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[3], st));
+  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_TRY(sync_status(g, st));
+  const DevCounters& c = *g->ctr_host;
+  if (c.err & kErrTimeout) return TC_ERR_TIMEOUT;
+  if (c.err & kErrOverflow) return TC_ERR_OVERFLOW;
+  if (c.err) return TC_ERR_CUDA;
+  *count = c.tri;
+  g->stats.triangles = c.tri;
+  g->stats.c1 = c.c1;
+  g->stats.c2 = c.c2;
+  g->stats.num_cover = c.num_cover;
+  cudaEventElapsedTime(&g->stats.ms_bfs, g->ev[0], g->ev[1]);
+  cudaEventElapsedTime(&g->stats.ms_cover, g->ev[1], g->ev[2]);
+  cudaEventElapsedTime(&g->stats.ms_intersect, g->ev[2], g->ev[3]);
+  cudaEventElapsedTime(&g->stats.ms_total, g->ev[0], g->ev[3]);
+  g->stats.ms_hash = 0.f;
+  if (c.items) cudaEventElapsedTime(&g->stats.ms_hash, g->ev[4], g->ev[3]);
+  g->stats.launches = g_launches - launches0;
+  g->stats.hash_items = c.items;
+  g->stats.hash_edges = c.num_large;
+  g->counted = true;
+  g->last_root = root;
+  return TC_OK;
+}
+
+tc_status tc_count_many(tc_graph* const* gs, const uint32_t* roots, size_t k, void* stream,
+                        uint64_t* counts) {
+  if (k == 0) return TC_OK;
+  if (!gs || !roots || !counts) return TC_ERR_INVALID_ARG;
+  for (size_t i = 0; i < k; ++i) {
+    if (!gs[i]) return TC_ERR_INVALID_ARG;
+    if (gs[i]->n > 0 && roots[i] >= gs[i]->n) return TC_ERR_INVALID_ARG;
+  }
+  std::vector<uint64_t> tmp(k);
+  for (size_t i = 0; i < k; ++i) TC_TRY(tc_count(gs[i], roots[i], stream, &tmp[i]));
+  for (size_t i = 0; i < k; ++i) counts[i] = tmp[i];
+  return TC_OK;
+}
+
+tc_status tc_get_levels(const tc_graph* g, int32_t* host_levels) {
+  if (!g || !host_levels) return TC_ERR_INVALID_ARG;
+  if (!g->counted) return TC_ERR_INVALID_ARG;
+  if (g->n == 0) return TC_OK;
+  TC_CUDA_TRY(cudaDeviceSynchronize());
+  TC_CUDA_TRY(cudaMemcpy(host_levels, g->level, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost));
+  return TC_OK;
+}
+
+tc_status tc_get_cover_edges(const tc_graph* g, uint64_t* num_cover, uint32_t* host_u,
+                             uint32_t* host_v) {
+  if (!g || !num_cover) return TC_ERR_INVALID_ARG;
+  if (!g->counted) return TC_ERR_INVALID_ARG;
+  *num_cover = g->stats.num_cover;
+  if (!host_u || !host_v || g->stats.num_cover == 0) return TC_OK;
+  TC_CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<uint2> tmp(g->stats.num_cover);
+  TC_CUDA_TRY(cudaMemcpy(tmp.data(), g->cover, sizeof(uint2) * tmp.size(), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < tmp.size(); ++i) {
+    host_u[i] = tmp[i].x;
+    host_v[i] = tmp[i].y;
+  }
+  return TC_OK;
+}
+
+tc_status tc_get_csr(const tc_graph* g, uint64_t* host_row_ptr, uint32_t* host_col) {
+  if (!g || !host_row_ptr || (!host_col && g->nnz)) return TC_ERR_INVALID_ARG;
+  TC_CUDA_TRY(cudaDeviceSynchronize());
+  TC_CUDA_TRY(cudaMemcpy(host_row_ptr, g->row_ptr, sizeof(uint64_t) * ((size_t)g->n + 1),
+                         cudaMemcpyDeviceToHost));
+  if (g->nnz)
+    TC_CUDA_TRY(cudaMemcpy(host_col, g->col, sizeof(uint32_t) * g->nnz, cudaMemcpyDeviceToHost));
+  return TC_OK;
+}
+
+tc_status tc_get_stats(const tc_graph* g, tc_stats* out) {
+  if (!g || !out) return TC_ERR_INVALID_ARG;
+  *out = g->stats;
+  return TC_OK;
+}
+
+const char* tc_status_string(tc_status s) {
+  switch (s) {
+    case TC_OK: return "TC_OK";
+    case TC_ERR_INVALID_ARG: return "TC_ERR_INVALID_ARG: invalid argument";
+    case TC_ERR_VERTEX_RANGE: return "TC_ERR_VERTEX_RANGE: edge endpoint >= num_vertices";
+    case TC_ERR_OOM: return "TC_ERR_OOM: device allocation failed";
+    case TC_ERR_CUDA: return "TC_ERR_CUDA: CUDA runtime error";
+    case TC_ERR_TIMEOUT: return "TC_ERR_TIMEOUT: bounded device wait expired";
+    case TC_ERR_OVERFLOW: return "TC_ERR_OVERFLOW: size beyond supported limits";
+  }
+  return "unknown tc_status";
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Internal declarations of libtc (CUDA, sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+constexpr int kWarp = 32;
+constexpr uint32_t kNoLevel = 0xFFFFFFFFu;  // level word of an unvisited vertex (-1)
+
+// Device-side error word values (bit flags, OR-ed by kernels).
+enum : uint32_t { kErrVertexRange = 1u, kErrTimeout = 2u, kErrOverflow = 4u };
+
+// Counters that kernels accumulate and the host reads back with one copy.
+struct DevCounters {
+  unsigned long long tri;        // T
+  unsigned long long c1;         // apex on another level
+  unsigned long long c2;         // apex on the same level
+  unsigned long long num_cover;  // |S|
+  unsigned long long num_large;  // cover edges sent to the owner-hash path
+  unsigned long long next_n;     // BFS: vertices discovered this step
+  unsigned long long next_m;     // BFS: sum of their degrees
+  unsigned long long scan_total; // total of the last device-wide scan
+  unsigned long long items;      // owner-hash work items
+  unsigned long long item_cursor;// dynamic work counter
+  unsigned long long unvisited;  // vertices still unvisited
+  unsigned int err;              // kErr* flags
+  unsigned int dmax;             // largest degree
+  unsigned int dmax_vertex;      // smallest id of largest degree
+  unsigned int pad;
+};
+
+// Scratch for the device-wide exclusive scan (reduce-then-scan, recursive).
+struct ScanScratch {
+  unsigned long long* sums = nullptr;  // block totals, all recursion levels
+  size_t capacity = 0;                 // entries in sums
+};
+
+}  // namespace tc
+
+// The opaque handle.  Every array is device memory owned by the handle.
+struct tc_graph {
+  uint32_t n = 0;
+  uint64_t m = 0;          // undirected edges
+  uint64_t nnz = 0;        // 2m
+  uint32_t d_max = 0;
+  uint32_t maxdeg_vertex = 0;
+  unsigned long long* row_ptr = nullptr;  // [n+1]
+  uint32_t* col = nullptr;                // [nnz]
+
+  // per-count state, sized at creation so a count allocates nothing
+  int32_t* level = nullptr;      // [n]
+  uint32_t* queue_a = nullptr;   // [n]  frontier queues
+  uint32_t* queue_b = nullptr;   // [n]
+  unsigned long long* qoff = nullptr;  // [n+1] frontier degree offsets
+  unsigned long long* ooff = nullptr;  // [n+1] owner bucket offsets
+  uint32_t* parent = nullptr;    // [n]  union-find parents (restart components)
+  uint32_t* fdeg = nullptr;      // [n]  degrees of frontier vertices
+  uint32_t* ocount = nullptr;    // [n]  cover edges per owner
+  uint32_t* ofill = nullptr;     // [n]  owner bucket fill cursors
+  unsigned long long* ioff = nullptr;  // [n+1] work-item offsets per owner
+  uint32_t* item_owner = nullptr;      // [item_cap] owner of each hash work item
+  unsigned long long item_cap = 0;
+  uint2* cover = nullptr;        // [m]  all cover edges (u < v)
+  uint2* large = nullptr;        // [m]  (owner, streamer) of owner-hash cover edges
+  uint32_t* ostream = nullptr;   // [m]  streamers bucketed by owner
+  tc::DevCounters* ctr = nullptr;      // device counters
+  tc::DevCounters* ctr_host = nullptr; // pinned mirror
+  tc::ScanScratch scan;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
+  tc_params params;
+  tc_stats stats;
+  bool counted = false;
+  uint32_t last_root = 0;
+};
+
+namespace tc {
+
+// ---- helpers shared by the .cu files ------------------------------------
+
+#define TC_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) {                               \
+      tc::set_last_cuda_error(_e);                         \
+      return (_e == cudaErrorMemoryAllocation) ? TC_ERR_OOM : TC_ERR_CUDA; \
+    }                                                      \
+  } while (0)
+
+#define TC_TRY(expr)                 \
+  do {                               \
+    tc_status _s = (expr);           \
+    if (_s != TC_OK) return _s;      \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e);
+
+// Kernel launches made by the library on this host thread (for tc_stats).
+extern thread_local uint32_t g_launches;
+#define TC_LAUNCHED() (++tc::g_launches)
+
+inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap = 1u << 20) {
+  uint64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+int num_sms();
+
+// Device-wide exclusive scan of `count` values (uint32 or uint64 input) into
+// uint64 offsets out[0..count]; out[count] holds the total.  `in` and `out`
+// may alias only for the uint64 variant.
+tc_status exclusive_scan_u32(const uint32_t* in, unsigned long long* out, uint64_t count,
+                             ScanScratch& s, cudaStream_t st);
+tc_status exclusive_scan_u64(const unsigned long long* in, unsigned long long* out,
+                             uint64_t count, ScanScratch& s, cudaStream_t st);
+size_t scan_scratch_entries(uint64_t max_count);
+
+// Phases (implemented in the .cu files of the same name).
+tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
+                    cudaStream_t st);
+tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st);
+tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
+
+// ---- device helpers -----------------------------------------------------
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Inclusive warp scan.
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (unsigned)o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan; all threads of the block call it.  `tmp` holds
+// blockDim.x / 32 + 1 entries.  Returns the exclusive prefix; *total gets the sum.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* tmp, T* total) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_inclusive_scan(v);
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? tmp[lane] : T(0);
+    T wi = warp_inclusive_scan(w);
+    if (lane < nw) tmp[lane] = wi - w;
+    if (lane == nw - 1) tmp[nw] = wi;
+  }
+  __syncthreads();
+  T out = tmp[warp] + inc - v;
+  *total = tmp[nw];
+  __syncthreads();
+  return out;
+}
+
+// Block-wide sum delivered to every thread. `tmp` holds blockDim.x/32 + 1 entries.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* tmp) {
+  T total;
+  block_exclusive_scan(v, tmp, &total);
+  return total;
+}
+
+}  // namespace tc
