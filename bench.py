@@ -171,14 +171,21 @@ def measured_peaks():
 # algorithmic bytes of the owner-hash kernel
 # ----------------------------------------------------------------------------
 
-def hash_kernel_bytes(rp, col, cu, cv, params) -> dict:
-    """Bytes the owner-hash kernel must move, from the graph and its cover set.
+SPLIT_MAX = 1 << 62  # every row is streamed level-split
 
-    Per hash-path cover edge {h, x} (h the owner, x the streamer): the part of
-    N(x) it streams (4 d(x)), its bucket entry (4) and x's row offsets (16).
-    Per work item (owner h, chunk, slice): the chunk of N(h) and those vertices'
-    levels (8 per entry) plus the owner's offsets (32).
+
+def hash_kernel_bytes(rp, col, level, cu, cv, params) -> dict:
+    """Bytes the owner-hash kernel must move, from the graph, levels and cover set.
+
+    Per owner-path cover edge {h, x} (h the owner: larger degree, ties larger id;
+    x the streamer), with v = max(h, x): the elements of N(x) that can count --
+    its neighbours on another level plus its same-level neighbours above v (the
+    whole row if d(x) > SPLIT_MAX) -- 4 bytes each, plus its bucket entry (4),
+    x's row offsets and split point (24) and the binary search for v (4 log2 d).
+    Per work item (owner h, slice of its cover edges): the row N(h) (4 per entry)
+    and the owner's offsets (32).
     """
+    n = rp.size - 1
     deg = np.diff(rp.astype(np.int64))
     du = deg[cu].astype(np.int64)
     dv = deg[cv].astype(np.int64)
@@ -189,17 +196,29 @@ def hash_kernel_bytes(rp, col, cu, cv, params) -> dict:
     du, dv = du[large], dv[large]
     v_owns = (dv > du) | ((dv == du) & (v > u))
     owner = np.where(v_owns, v, u)
-    d_stream = np.where(v_owns, du, dv)
-    per_edge = 4 * d_stream + 20
+    x = np.where(v_owns, u, v)
+    vmax = np.maximum(u, v)
+    # same-level neighbours of every vertex as a sorted key list (row << 32 | id)
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    same = level[rows] == level[col]
+    keys = (rows[same] << 32) | col[same].astype(np.int64)
+    same_deg = np.bincount(rows[same], minlength=n).astype(np.int64)
+    del rows, same
+    start = np.searchsorted(keys, x << 32)
+    upto_v = np.searchsorted(keys, (x << 32) | (vmax + 1))
+    above = same_deg[x] - (upto_v - start)
+    dx = deg[x]
+    streamed = np.where(dx > SPLIT_MAX, dx, (dx - same_deg[x]) + above)
+    log_d = np.ceil(np.log2(np.maximum(dx, 2)))
+    per_edge = 4 * streamed + 32 + 4 * log_d.astype(np.int64)
     owners, oc = np.unique(owner, return_counts=True)
     dh = deg[owners]
-    chunk, per_item = params["hash_chunk"], params["edges_per_item"]
+    per_item = params["edges_per_item"]
     slices = (oc + per_item - 1) // per_item
-    chunks = (dh + chunk - 1) // chunk
-    items = int((slices * chunks).sum())
-    per_owner = slices * (8 * dh) + 32 * slices * chunks
+    per_owner = slices * (4 * dh + 32)
     return {"bytes": int(per_edge.sum() + per_owner.sum()), "edges": int(large.sum()),
-            "items": items, "sum_stream_deg": int(d_stream.sum())}
+            "items": int(slices.sum()), "streamed_elements": int(streamed.sum()),
+            "row_elements": int(dx.sum())}
 
 
 def kernel_source_sha() -> str:
@@ -381,7 +400,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (owner-hash intersection), algorithmic bytes
     rp, col = g.csr()
     cu, cv = g.cover_edges()
-    hb = hash_kernel_bytes(rp, col, cu, cv, params)
+    hb = hash_kernel_bytes(rp, col, g.levels(), cu, cv, params)
     deg = np.diff(rp.astype(np.int64))
     survey_bytes = int(24 * m + 12 * spec.n + 16 * n_cover +
                        4 * (deg[cu].sum() + deg[cv].sum()) + 4 * (st["c1"] + st["c2"]))
@@ -438,7 +457,9 @@ def run_ours(args, world, rank, local):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "alg_bytes_per_launch": hb["bytes"], "hash_edges": hb["edges"],
-                     "hash_items": hb["items"], "survey_alg_bytes_per_count": survey_bytes},
+                     "hash_items": hb["items"], "streamed_elements": hb["streamed_elements"],
+                     "streamer_row_elements": hb["row_elements"],
+                     "survey_alg_bytes_per_count": survey_bytes},
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 8 * E,
                 "d2h_bytes_per_step": 8, "seconds_per_step": e2e_max},
         "gpu_launches": launches,

@@ -152,8 +152,8 @@ tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v);
  */
 typedef struct tc_params {
   uint32_t small_max_degree; /* cover edges with both degrees <= this use the direct merge */
-  uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (power of 2) */
-  uint32_t edges_per_item;   /* cover edges per hash work item */
+  uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (power of 2, 32..16384) */
+  uint32_t edges_per_item;   /* cover edges per hash work item (1..512) */
   uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
   uint32_t reserved[3];

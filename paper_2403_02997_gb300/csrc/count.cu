@@ -2,23 +2,34 @@
 // (Section "Cover-Edge Triangle Counting"), computed in the parallel shape of
 // Algorithm CETC-SM.
 //
+// Counting rule (Algorithm CETC-Seq): for a cover edge {u, v}, u < v, a common
+// neighbour w counts when L(w) != L(u) (c1 of Algorithm CETC-SM), or when
+// L(w) == L(u) and v < w.  Every path below tallies c1 and c2' = the number of
+// same-level common neighbours with v < w, so T = c1 + c2'.  The CETC-SM
+// statistic c2 (all same-level common neighbours) equals 3 c2': a same-level
+// apex exists only in a triangle with three horizontal edges (Lemma "HE2"),
+// which each of its three cover edges sees, and exactly one of them, the edge
+// of its two smallest vertices, sees with the apex above v.
+//
 // k_cover        one thread per adjacency entry (u, v): a horizontal edge with
 //                u < v (L(u) == L(v), Definition "BFS-Edge") is a cover edge
-//                (Theorem "Cover-Edge Set Generation").  It is appended to the
-//                cover list.  If both degrees are <= small_max_degree the thread
-//                intersects the two rows itself (the two-pointer merge of
-//                Algorithm EMP); otherwise the edge goes to the endpoint of
-//                larger degree, its "owner", for the hash path.
-// k_bucket       groups the hash-path edges by owner (counting sort).
-// k_owner_hash   one CTA per work item (owner h, chunk c of N(h), slice of h's
-//                cover edges): chunk c is loaded into a shared-memory hash table
-//                (the scatter / probe / clear scheme of Algorithm EHP), tagged
-//                per entry with L(w) == L(h); each cover edge {h, x} then
-//                streams the part of N(x) inside the chunk's id range through
-//                the table.  Each common neighbour w is counted by the rule of
-//                Algorithm CETC-Seq: when L(w) != L(u), or L(w) == L(u) and
-//                v < w, with u < v the edge's endpoints; c1 / c2 of Algorithm
-//                CETC-SM are kept beside T.
+//                (Theorem "Cover-Edge Set Generation") and joins the cover
+//                list.  If both degrees are <= small_max_degree the thread merges
+//                the two rows itself (two pointers, Algorithm EMP); otherwise the
+//                edge goes to its endpoint of larger degree, the "owner".
+// k_level_split  per row x: a copy of N(x) reordered as [neighbours on another
+//                level | neighbours on L(x)], each part ascending (a stable
+//                partition; rows up to kSplitMax by one warp, longer rows in
+//                tiles of kSplitTile by k_split_tile_*).  A streamer then skips
+//                its same-level neighbours w <= v, which can never count.
+// k_bucket       groups the owner-path edges by owner (counting sort).
+// k_owner_hash   one CTA per work item (owner h, slice of h's cover edges):
+//                N(h) is taken in chunks; each chunk goes into a shared-memory
+//                hash table (the scatter / probe scheme of Algorithm EHP; two-
+//                choice cuckoo buckets of 4 behind a one-bit-per-slot filter:
+//                a miss costs one 4-byte load, a hit two 16-byte loads), and
+//                every edge {h, x} of the slice streams its segments of N(x) up
+//                to the chunk's largest id through it.
 // Per-thread counts are reduced by warp shuffles and one atomic per CTA.
 #include "tc_internal.cuh"
 
@@ -29,8 +40,16 @@ namespace {
 constexpr int kCoverBlock = 256;
 constexpr int kCoverEntriesPerBlock = 2048;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kSameLevel = 0x80000000u;
 constexpr int kHashBlock = 512;
+constexpr int kStreamUnroll = 4;
+constexpr int kMaxEdgesPerItem = 512;
+constexpr uint32_t kSplitMax = 4096;    // rows longer than this are split in tiles
+constexpr uint32_t kSplitTile = 4096;   // entries per tile of a long row
+constexpr int kTileBlock = 512;         // threads per tile block (8 entries each)
+constexpr uint32_t kHashA = 2654435761u;  // multiplicative hashing constants (odd)
+constexpr uint32_t kHashB = 0x85EBCA77u;
+constexpr uint32_t kHashC = 0xC2B2AE35u;
+constexpr int kCuckooRounds = 96;
 
 __device__ __forceinline__ void warp_append_pair(bool take, uint2 value, uint2* list,
                                                  unsigned long long* len) {
@@ -54,41 +73,29 @@ __device__ __forceinline__ uint32_t row_of(const unsigned long long* row_ptr, ui
   return lo;
 }
 
+// c1 and c2' of one thread (see the file comment).
 struct Tally {
-  unsigned long long t = 0, c1 = 0, c2 = 0;
-  __device__ __forceinline__ void add(bool same, uint32_t v, uint32_t w) {
-    if (!same) {
-      ++t;
-      ++c1;
-    } else {
-      ++c2;
-      if (v < w) ++t;
-    }
-  }
+  unsigned long long c1 = 0, c2c = 0;
 };
 
 __device__ __forceinline__ void flush_tally(Tally tl, DevCounters* ctr) {
-  __shared__ unsigned long long red[3][32];
-  tl.t = warp_sum(tl.t);
+  __shared__ unsigned long long red[2][32];
   tl.c1 = warp_sum(tl.c1);
-  tl.c2 = warp_sum(tl.c2);
+  tl.c2c = warp_sum(tl.c2c);
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (lane == 0) {
-    red[0][warp] = tl.t;
-    red[1][warp] = tl.c1;
-    red[2][warp] = tl.c2;
+    red[0][warp] = tl.c1;
+    red[1][warp] = tl.c2c;
   }
   __syncthreads();
   if (warp == 0) {
-    unsigned long long a = lane < nw ? red[0][lane] : 0, b = lane < nw ? red[1][lane] : 0,
-                       c = lane < nw ? red[2][lane] : 0;
+    unsigned long long a = lane < nw ? red[0][lane] : 0, b = lane < nw ? red[1][lane] : 0;
     a = warp_sum(a);
     b = warp_sum(b);
-    c = warp_sum(c);
     if (lane == 0) {
-      if (a) atomicAdd(&ctr->tri, a);
-      if (b) atomicAdd(&ctr->c1, b);
-      if (c) atomicAdd(&ctr->c2, c);
+      if (a + b) atomicAdd(&ctr->tri, a + b);
+      if (a) atomicAdd(&ctr->c1, a);
+      if (b) atomicAdd(&ctr->c2, 3ull * b);
     }
   }
 }
@@ -134,7 +141,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
               while (x < eu && y < ev) {
                 const uint32_t a = col[x], c = col[y];
                 if (a == c) {
-                  tl.add(level[a] == lu, v, a);
+                  if (level[a] != lu) ++tl.c1;
+                  else if (v < a) ++tl.c2c;
                   ++x;
                   ++y;
                 } else if (a < c) {
@@ -159,6 +167,142 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
   flush_tally(tl, ctr);
 }
 
+// One warp per row of degree <= kSplitMax (grid-stride).  Pass 1 counts the
+// neighbours on another level; pass 2 writes both parts in order with ballot
+// ranks.  Longer rows are left to the tile kernels below.
+__global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
+                              const uint32_t* __restrict__ col, const int32_t* __restrict__ level,
+                              uint32_t n, uint32_t* __restrict__ lcol,
+                              unsigned long long* __restrict__ lsplit) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t warps = (uint64_t)gridDim.x * blockDim.x / 32;
+  for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; x < n; x += warps) {
+    const unsigned long long b = row_ptr[x], e = row_ptr[x + 1];
+    if (e - b > kSplitMax) continue;
+    if (e == b) {
+      if (lane == 0) lsplit[x] = b;
+      continue;
+    }
+    const int32_t lx = level[x];
+    unsigned long long other = 0;
+    for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+      const unsigned long long j = j0 + lane;
+      const bool o = j < e && level[col[j]] != lx;
+      other += __popc(__ballot_sync(0xffffffffu, o));
+    }
+    unsigned long long po = b, ps = b + other;
+    for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+      const unsigned long long j = j0 + lane;
+      uint32_t w = 0;
+      const bool valid = j < e;
+      bool o = false;
+      if (valid) {
+        w = col[j];
+        o = level[w] != lx;
+      }
+      const unsigned mo = __ballot_sync(0xffffffffu, valid && o);
+      const unsigned ms = __ballot_sync(0xffffffffu, valid && !o);
+      if (valid) {
+        if (o) lcol[po + __popc(mo & lt)] = w;
+        else lcol[ps + __popc(ms & lt)] = w;
+      }
+      po += __popc(mo);
+      ps += __popc(ms);
+    }
+    if (lane == 0) lsplit[x] = b + other;
+  }
+}
+
+// Tiles of the rows longer than kSplitMax: tiles[x] = ceil(d(x) / kSplitTile).
+__global__ void k_split_tiles(const unsigned long long* __restrict__ row_ptr, uint32_t n,
+                              uint32_t* __restrict__ tiles) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = row_ptr[x + 1] - row_ptr[x];
+    tiles[x] = d > kSplitMax ? (uint32_t)((d + kSplitTile - 1) / kSplitTile) : 0u;
+  }
+}
+
+__global__ void k_tile_rows(const unsigned long long* __restrict__ toff, uint32_t n,
+                            uint32_t* __restrict__ tile_row) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x)
+    for (unsigned long long t = toff[x]; t < toff[x + 1]; ++t) tile_row[t] = (uint32_t)x;
+}
+
+// Block per tile: number of entries on another level than the row's vertex.
+__global__ void __launch_bounds__(kTileBlock) k_split_tile_count(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, const uint32_t* __restrict__ tile_row,
+    const unsigned long long* __restrict__ toff, uint32_t* __restrict__ tcnt) {
+  __shared__ uint32_t tmp[kTileBlock / 32 + 1];
+  const uint32_t t = blockIdx.x;
+  const uint32_t x = tile_row[t];
+  const unsigned long long b = row_ptr[x], e = row_ptr[x + 1];
+  const unsigned long long tb = b + (unsigned long long)(t - toff[x]) * kSplitTile;
+  const unsigned long long te = min(e, tb + kSplitTile);
+  const int32_t lx = level[x];
+  uint32_t c = 0;
+  for (unsigned long long j = tb + threadIdx.x; j < te; j += kTileBlock) c += level[col[j]] != lx;
+  c = block_sum(c, tmp);
+  if (threadIdx.x == 0) tcnt[t] = c;
+}
+
+// Block per tile: writes the tile's entries to their places in both parts.
+// Thread i holds the tile's entries 8i..8i+7 (input order), so block-wide
+// exclusive scans of the per-thread counts give stable ranks.
+__global__ void __launch_bounds__(kTileBlock) k_split_tile_write(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, const uint32_t* __restrict__ tile_row,
+    const unsigned long long* __restrict__ toff, const uint32_t* __restrict__ tcnt,
+    uint32_t* __restrict__ lcol, unsigned long long* __restrict__ lsplit) {
+  constexpr int kPer = kSplitTile / kTileBlock;
+  __shared__ unsigned long long tmp[kTileBlock / 32 + 1];
+  const uint32_t t = blockIdx.x;
+  const uint32_t x = tile_row[t];
+  const unsigned long long b = row_ptr[x], e = row_ptr[x + 1];
+  const unsigned long long t0 = toff[x], nt = toff[x + 1] - t0, k = t - t0;
+  const unsigned long long tb = b + k * kSplitTile;
+  const int32_t lx = level[x];
+  // other-level entries of the earlier tiles, and of the whole row
+  unsigned long long before = 0, all = 0;
+  for (unsigned long long q = threadIdx.x; q < nt; q += kTileBlock) {
+    const unsigned long long c = tcnt[t0 + q];
+    all += c;
+    if (q < k) before += c;
+  }
+  before = block_sum(before, tmp);
+  all = block_sum(all, tmp);
+  uint32_t w[kPer];
+  unsigned flags = 0, mine = 0, valid = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const unsigned long long j = tb + (unsigned long long)threadIdx.x * kPer + i;
+    w[i] = 0;
+    if (j < e) {
+      w[i] = col[j];
+      valid |= 1u << i;
+      if (level[w[i]] != lx) {
+        flags |= 1u << i;
+        ++mine;
+      }
+    }
+  }
+  unsigned long long tot;
+  unsigned long long po = block_exclusive_scan((unsigned long long)mine, tmp, &tot);
+  unsigned long long ps = block_exclusive_scan((unsigned long long)(__popc(valid) - mine), tmp, &tot);
+  po += b + before;
+  ps += b + all + (k * kSplitTile - before);
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    if (!(valid & (1u << i))) continue;
+    if (flags & (1u << i)) lcol[po++] = w[i];
+    else lcol[ps++] = w[i];
+  }
+  if (k == 0 && threadIdx.x == 0) lsplit[x] = b + all;
+}
+
 __global__ void k_bucket(const uint2* __restrict__ large, unsigned long long count,
                          const unsigned long long* __restrict__ ooff, uint32_t* __restrict__ ofill,
                          uint32_t* __restrict__ ostream) {
@@ -170,27 +314,12 @@ __global__ void k_bucket(const uint2* __restrict__ large, unsigned long long cou
   }
 }
 
-// Work items per owner: ceil(d(h) / chunk) chunks x ceil(ocount / edges_per_item) slices.
-__global__ void k_item_counts(const unsigned long long* __restrict__ row_ptr,
-                              const uint32_t* __restrict__ ocount, uint32_t n, uint32_t chunk,
-                              uint32_t per_item, uint32_t* __restrict__ icount,
-                              DevCounters* ctr) {
+// Work items per owner h: ceil(ocount[h] / edges_per_item) slices of its cover edges.
+__global__ void k_item_counts(const uint32_t* __restrict__ ocount, uint32_t n, uint32_t per_item,
+                              uint32_t* __restrict__ icount) {
   for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n;
-       h += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t oc = ocount[h];
-    unsigned long long items = 0;
-    if (oc) {
-      const unsigned long long d = row_ptr[h + 1] - row_ptr[h];
-      const unsigned long long chunks = (d + chunk - 1) / chunk;
-      const unsigned long long slices = (oc + per_item - 1) / per_item;
-      items = chunks * slices;
-      if (items > 0xFFFFFFFFull) {  // tunables too fine for this owner: report, skip
-        atomicOr(&ctr->err, kErrOverflow);
-        items = 0;
-      }
-    }
-    icount[h] = (uint32_t)items;
-  }
+       h += (uint64_t)gridDim.x * blockDim.x)
+    icount[h] = (ocount[h] + per_item - 1) / per_item;
 }
 
 __global__ void k_item_owner(const unsigned long long* __restrict__ ioff, uint32_t n,
@@ -200,41 +329,141 @@ __global__ void k_item_owner(const unsigned long long* __restrict__ ioff, uint32
     for (unsigned long long i = ioff[h]; i < ioff[h + 1]; ++i) item_owner[i] = (uint32_t)h;
 }
 
-// First index in the sorted range col[a, b) whose value is >= t (warp-wide
-// 32-ary search; all lanes get the answer).
-__device__ __forceinline__ unsigned long long warp_lower_bound(const uint32_t* __restrict__ col,
-                                                               unsigned long long a,
-                                                               unsigned long long b, uint32_t t) {
-  const unsigned lane = lane_id();
-  while (b - a > 32) {
-    const unsigned long long step = (b - a + 31) / 32;
-    const unsigned long long idx = a + lane * step;
-    const uint32_t val = idx < b ? col[idx] : 0xFFFFFFFFu;
-    const unsigned k = __popc(__ballot_sync(0xffffffffu, val < t));
-    if (k == 0) return a;
-    const unsigned long long na = a + (k - 1) * step + 1;
-    const unsigned long long nb = a + (unsigned long long)k * step;
-    a = na;
-    if (nb < b) b = nb;
+// ---- the owner-hash kernel ----------------------------------------------
+
+// Two-choice cuckoo hashing with buckets of 4 slots in shared memory, behind a
+// bitmap filter of 16 bits per entry (one hash; a miss is rejected by one load
+// with probability about 15/16).
+struct Cuckoo {
+  uint32_t* table;   // 4 * 2^(32 - shift) slots
+  uint32_t* filter;  // 2^(32 - fshift) bits
+  uint32_t shift;    // 32 - log2(buckets)
+  uint32_t fshift;   // 32 - log2(filter bits)
+  __device__ __forceinline__ uint32_t b1(uint32_t w) const { return (w * kHashA) >> shift; }
+  __device__ __forceinline__ uint32_t b2(uint32_t w) const {
+    const uint32_t a = (w * kHashA) >> shift, b = (w * kHashB) >> shift;
+    return a == b ? (b ^ 1u) : b;
   }
-  const unsigned long long idx = a + lane;
-  const uint32_t val = idx < b ? col[idx] : 0xFFFFFFFFu;
-  return a + __popc(__ballot_sync(0xffffffffu, val < t));
+  __device__ __forceinline__ uint32_t fbit(uint32_t w) const { return (w * kHashC) >> fshift; }
+  // Insert w; false if it could not be placed (the caller falls back).
+  __device__ __forceinline__ bool insert(uint32_t w, unsigned salt) const {
+    const uint32_t f = fbit(w);
+    atomicOr(&filter[f >> 5], 1u << (f & 31));
+    uint32_t cur = w;
+    for (int it = 0; it < kCuckooRounds; ++it) {
+      const uint32_t a = b1(cur), b = b2(cur);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        uint32_t* slot = &table[4 * (t < 4 ? a : b) + (t & 3)];
+        if (*slot == kEmpty && atomicCAS(slot, kEmpty, cur) == kEmpty) return true;
+      }
+      const uint32_t victim = ((it + salt) & 1) ? b : a;
+      cur = atomicExch(&table[4 * victim + ((it * 5u + salt) & 3u)], cur);
+      if (cur == kEmpty) return true;
+    }
+    return false;
+  }
+  __device__ __forceinline__ bool contains(uint32_t w) const {
+    const uint32_t f = fbit(w);
+    if (!((filter[f >> 5] >> (f & 31)) & 1u)) return false;
+    const uint4 p = reinterpret_cast<const uint4*>(table)[b1(w)];
+    const uint4 q = reinterpret_cast<const uint4*>(table)[b2(w)];
+    return (p.x == w) | (p.y == w) | (p.z == w) | (p.w == w) | (q.x == w) | (q.y == w) |
+           (q.z == w) | (q.w == w);
+  }
+};
+
+// Sorted-array lookup, used for a chunk whose cuckoo build failed.
+__device__ __forceinline__ bool sorted_contains(const uint32_t* a, uint32_t len, uint32_t w) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < w) lo = mid + 1; else hi = mid;
+  }
+  return lo < len && a[lo] == w;
 }
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t w, uint32_t mask) {
-  return (w * 2654435761u) & mask;
+__device__ __forceinline__ void load_block(const uint32_t* __restrict__ arr, unsigned long long cur,
+                                           unsigned long long end, uint32_t (&w)[kStreamUnroll]) {
+  const unsigned lane = lane_id();
+  const unsigned long long left = end - cur;
+  const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
+#pragma unroll
+  for (int u = 0; u < kStreamUnroll; ++u) {
+    const uint32_t j = lane + 32u * u;
+    w[u] = j < rem ? __ldg(arr + cur + j) : kEmpty;
+  }
 }
 
+// The warp streams arr[cur, end) up to the first id above hi (when bounded),
+// looking every element up in the chunk; returns the new cursor.  A hit counts
+// to c1 for a segment of other-level neighbours (kSame = false) and to c2' for
+// the same-level neighbours above v (kSame = true).  The next block of
+// kStreamUnroll x 32 elements is loaded before the current one is looked up.
+template <bool kSame>
+__device__ __forceinline__ unsigned long long stream_segment(
+    const uint32_t* __restrict__ arr, unsigned long long cur, const unsigned long long end,
+    const bool bounded, const uint32_t hi, const Cuckoo& ck, const bool sorted,
+    const uint32_t sorted_len, uint32_t& hits) {
+  if (cur >= end) return end;
+  const unsigned lane = lane_id();
+  uint32_t w[kStreamUnroll];
+  load_block(arr, cur, end, w);
+  for (;;) {
+    const unsigned long long next = cur + 32ull * kStreamUnroll;
+    const bool more = next < end;
+    uint32_t wn[kStreamUnroll];
+    if (more) load_block(arr, next, end, wn);
+    const unsigned long long left = end - cur;
+    const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const uint32_t j = lane + 32u * u;
+      const bool in = j < rem && (!bounded || w[u] <= hi);
+      const unsigned stop = __ballot_sync(0xffffffffu, !in);
+      const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
+      if (lane < take) hits += sorted ? sorted_contains(ck.table, sorted_len, w[u]) : ck.contains(w[u]);
+      if (stop) return cur + 32ull * u + take;
+    }
+    if (!more) return end;
+    cur = next;
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) w[u] = wn[u];
+  }
+}
+
+// First index in arr[a, b) (sorted) with arr[i] >= t.
+__device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __restrict__ arr,
+                                                              unsigned long long a,
+                                                              unsigned long long b, uint32_t t) {
+  while (a < b) {
+    const unsigned long long mid = a + (b - a) / 2;
+    if (arr[mid] < t) a = mid + 1; else b = mid;
+  }
+  return a;
+}
+
+// Work item = (owner h, slice of h's cover edges).  N(h) is taken in chunks of
+// `chunk` entries; per chunk the table is rebuilt and every edge of the slice
+// streams both parts of its level-split row -- all neighbours on another level,
+// and the same-level neighbours above v -- from the part's cursor up to the
+// chunk's largest id (rows are sorted: cursors only move forward, and each
+// streamed element is looked up in exactly one chunk; the last chunk takes the
+// rest).  Warps take edges one at a time from a shared counter.
 __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-    const int32_t* __restrict__ level, uint32_t n, const unsigned long long* __restrict__ ooff,
-    const uint32_t* __restrict__ ostream, const unsigned long long* __restrict__ ioff,
-    const uint32_t* __restrict__ item_owner, unsigned long long nitems, uint32_t chunk,
-    uint32_t per_item, DevCounters* ctr) {
-  extern __shared__ uint32_t table[];
+    const uint32_t* __restrict__ lcol, const unsigned long long* __restrict__ lsplit,
+    const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
+    const unsigned long long* __restrict__ ioff, const uint32_t* __restrict__ item_owner,
+    unsigned long long nitems, uint32_t chunk, uint32_t per_item, DevCounters* ctr) {
+  extern __shared__ uint4 table4[];
   __shared__ unsigned long long s_item;
-  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ uint32_t s_next, s_fail;
+  __shared__ unsigned long long s_a[kMaxEdgesPerItem], s_ae[kMaxEdgesPerItem];
+  __shared__ unsigned long long s_b[kMaxEdgesPerItem], s_be[kMaxEdgesPerItem];
+  uint32_t* table = reinterpret_cast<uint32_t*>(table4);
+  uint32_t* filter = table + 2 * chunk;
+  const unsigned lane = lane_id();
   Tally tl;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctr->item_cursor, 1ull);
@@ -243,54 +472,64 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     if (item >= nitems) break;
     const uint32_t h = item_owner[item];
     const unsigned long long hb = row_ptr[h], he = row_ptr[h + 1];
-    const unsigned long long dh = he - hb;
-    const uint32_t chunks = (uint32_t)((dh + chunk - 1) / chunk);
-    const unsigned long long local = item - ioff[h];
-    const uint32_t c = (uint32_t)(local % chunks);
-    const unsigned long long s = local / chunks;
-    const unsigned long long cb = hb + (unsigned long long)c * chunk;
-    const unsigned long long ce = min(he, cb + chunk);
-    const uint32_t lo_id = col[cb], hi_id = col[ce - 1];
-    const int32_t lh = level[h];
-    const unsigned long long eb = ooff[h] + s * per_item;
-    const unsigned long long ee = min(ooff[h + 1], eb + per_item);
-
-    // table size for this chunk: a power of two >= 2 * entries (load <= 1/2)
-    uint32_t cap = 64;
-    while (cap < 2 * (uint32_t)(ce - cb)) cap <<= 1;
-    const uint32_t mask = cap - 1;
-    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = kEmpty;
-    __syncthreads();
-    for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x) {
-      const uint32_t w = col[j];
-      const uint32_t key = w | (level[w] == lh ? kSameLevel : 0u);
-      uint32_t slot = hash_slot(w, mask);
-      while (atomicCAS(&table[slot], kEmpty, key) != kEmpty) slot = (slot + 1) & mask;
-    }
-    __syncthreads();
-    for (unsigned long long e = eb + warp; e < ee; e += nw) {
-      const uint32_t x = ostream[e];
+    const uint32_t chunks = (uint32_t)((he - hb + chunk - 1) / chunk);
+    const unsigned long long eb = ooff[h] + (item - ioff[h]) * per_item;
+    const uint32_t ne = (uint32_t)min((unsigned long long)per_item, ooff[h + 1] - eb);
+    for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x) {
+      const uint32_t x = ostream[eb + i];
       const uint32_t v = x > h ? x : h;
-      unsigned long long xb = row_ptr[x], xe = row_ptr[x + 1];
-      if (chunks > 1) {
-        xb = warp_lower_bound(col, xb, xe, lo_id);
-        xe = warp_lower_bound(col, xb, xe, hi_id + 1);
-      }
-      for (unsigned long long j = xb + lane; j < xe; j += 32) {
-        const uint32_t w = col[j];
-        uint32_t slot = hash_slot(w, mask);
-        for (;;) {
-          const uint32_t k = table[slot];
-          if (k == kEmpty) break;
-          if ((k & ~kSameLevel) == w) {
-            tl.add((k & kSameLevel) != 0, v, w);
-            break;
-          }
-          slot = (slot + 1) & mask;
-        }
-      }
+      const unsigned long long sp = lsplit[x], xe = row_ptr[x + 1];
+      s_a[i] = row_ptr[x];
+      s_ae[i] = sp;
+      s_b[i] = lower_bound_u32(lcol, sp, xe, v + 1);
+      s_be[i] = xe;
     }
-    __syncthreads();
+    for (uint32_t c = 0; c < chunks; ++c) {
+      const unsigned long long cb = hb + (unsigned long long)c * chunk;
+      const unsigned long long ce = min(he, cb + chunk);
+      const uint32_t entries = (uint32_t)(ce - cb);
+      const bool bounded = c + 1 < chunks;
+      const uint32_t hi_id = bounded ? col[ce - 1] : kEmpty;
+      // buckets: a power of two >= entries / 2 (4 slots each: load <= 1/2), >= 16;
+      // filter: a power of two >= 16 bits per entry, >= 1024 bits
+      uint32_t bbits = 4, fbits = 10;
+      while ((4u << bbits) < 2 * entries) ++bbits;
+      while ((1u << fbits) < 16 * entries) ++fbits;
+      const Cuckoo ck{table, filter, 32u - bbits, 32u - fbits};
+      for (uint32_t i = threadIdx.x; i < (4u << bbits); i += blockDim.x) table[i] = kEmpty;
+      for (uint32_t i = threadIdx.x; i < (1u << (fbits - 5)); i += blockDim.x) filter[i] = 0u;
+      if (threadIdx.x == 0) {
+        s_next = 0;
+        s_fail = 0;
+      }
+      __syncthreads();
+      for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x)
+        if (!ck.insert(col[j], threadIdx.x)) s_fail = 1;
+      __syncthreads();
+      const bool sorted = s_fail != 0;
+      if (sorted) {  // rare: keep the chunk as a sorted array instead
+        for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) table[i] = col[cb + i];
+        __syncthreads();
+      }
+      for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(&s_next, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= ne) break;
+        uint32_t c1 = 0, c2c = 0;
+        const unsigned long long a =
+            stream_segment<false>(lcol, s_a[i], s_ae[i], bounded, hi_id, ck, sorted, entries, c1);
+        const unsigned long long b =
+            stream_segment<true>(lcol, s_b[i], s_be[i], bounded, hi_id, ck, sorted, entries, c2c);
+        if (lane == 0) {
+          s_a[i] = a;
+          s_b[i] = b;
+        }
+        tl.c1 += c1;
+        tl.c2c += c2c;
+      }
+      __syncthreads();
+    }
   }
   flush_tally(tl, ctr);
 }
@@ -316,13 +555,31 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaStreamSynchronize(st));
   const unsigned long long nlarge = g->ctr_host->num_large;
   if (nlarge == 0) return TC_OK;
+  // level-split rows: short rows by warps, long rows in tiles
+  k_level_split<<<sms * 16, 256, 0, st>>>(g->row_ptr, g->col, g->level, n, g->lcol, g->lsplit); TC_LAUNCHED();
+  if (g->d_max > kSplitMax) {
+    k_split_tiles<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->row_ptr, n, g->fdeg); TC_LAUNCHED();
+    TC_TRY(exclusive_scan_u32(g->fdeg, g->ioff, n, g->scan, st));
+    TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr_host->scan_total, g->ioff + n, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st));
+    TC_CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned long long ntiles = g->ctr_host->scan_total;
+    if (ntiles > g->tile_cap) return TC_ERR_OVERFLOW;
+    if (ntiles > 0) {
+      k_tile_rows<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->tile_row); TC_LAUNCHED();
+      k_split_tile_count<<<(unsigned)ntiles, kTileBlock, 0, st>>>(g->row_ptr, g->col, g->level,
+                                                                 g->tile_row, g->ioff, g->tile_cnt); TC_LAUNCHED();
+      k_split_tile_write<<<(unsigned)ntiles, kTileBlock, 0, st>>>(g->row_ptr, g->col, g->level,
+                                                                 g->tile_row, g->ioff, g->tile_cnt,
+                                                                 g->lcol, g->lsplit); TC_LAUNCHED();
+    }
+  }
   TC_CUDA_TRY(cudaMemsetAsync(g->ofill, 0, sizeof(uint32_t) * n, st));
   k_bucket<<<grid_for(nlarge, 256, sms * 16), 256, 0, st>>>(g->large, nlarge, g->ooff, g->ofill,
                                                            g->ostream); TC_LAUNCHED();
   const uint32_t chunk = g->params.hash_chunk;
   const uint32_t per_item = g->params.edges_per_item;
-  k_item_counts<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->row_ptr, g->ocount, n, chunk,
-                                                           per_item, g->fdeg, g->ctr); TC_LAUNCHED();
+  k_item_counts<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ocount, n, per_item, g->fdeg); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_TRY(exclusive_scan_u32(g->fdeg, g->ioff, n, g->scan, st));
   TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr->items, g->ioff + n, sizeof(unsigned long long),
@@ -341,8 +598,8 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
     g->item_cap = want;
   }
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
-  const uint32_t cap = 2 * chunk;
-  const size_t smem = sizeof(uint32_t) * cap;
+  // table: 2 * chunk slots (buckets of 4, load <= 1/2) + filter: 16 bits per entry
+  const size_t smem = sizeof(uint32_t) * (2 * (size_t)chunk + (size_t)chunk / 2 + 32);
   TC_CUDA_TRY(cudaFuncSetAttribute(k_owner_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   int per_sm = 0;
@@ -351,7 +608,7 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   unsigned grid = (unsigned)(sms * per_sm);
   if (nitems < grid) grid = (unsigned)nitems;
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
-  k_owner_hash<<<grid, kHashBlock, smem, st>>>(g->row_ptr, g->col, g->level, n, g->ooff,
+  k_owner_hash<<<grid, kHashBlock, smem, st>>>(g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff,
                                               g->ostream, g->ioff, g->item_owner, nitems, chunk,
                                               per_item, g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());

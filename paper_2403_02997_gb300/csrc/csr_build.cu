@@ -271,7 +271,11 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
         cudaMemsetAsync(g->row_ptr, 0, sizeof(unsigned long long) * ((size_t)n + 1), st);
         break;
       }
-      if (cudaMalloc(&g->col, sizeof(uint32_t) * nnz) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      // padded to a multiple of 4 entries plus 4, so 16-byte loads of any
+      // aligned quad that starts inside the array stay inside the allocation
+      const size_t col_alloc = ((size_t)nnz + 7) & ~(size_t)3;
+      if (cudaMalloc(&g->col, sizeof(uint32_t) * col_alloc) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      cudaMemsetAsync(g->col + nnz, 0, sizeof(uint32_t) * (col_alloc - nnz), st);
       k_dedup_write<<<(unsigned)ndb, kDedupBlock, 0, st>>>(keys_a, N, kb, n, hoff, hoff + ndb, g->col,
                                                            g->row_ptr); TC_LAUNCHED();
     } while (0);

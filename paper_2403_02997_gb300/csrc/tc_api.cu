@@ -46,7 +46,8 @@ void free_graph(tc_graph* g) {
   if (!g) return;
   void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
                   g->ooff,    g->ioff,  g->parent, g->fdeg,    g->ocount,  g->ofill,
-                  g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums};
+                  g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums,
+                  g->lcol,    g->lsplit, g->tile_row, g->tile_cnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -70,6 +71,12 @@ tc_status alloc_count_state(tc_graph* g) {
   TC_TRY(dalloc(&g->cover, m));
   TC_TRY(dalloc(&g->large, m));
   TC_TRY(dalloc(&g->ostream, m));
+  TC_TRY(dalloc(&g->lcol, g->nnz));
+  TC_TRY(dalloc(&g->lsplit, n));
+  // tiles of rows longer than 4096 entries, 4096 per tile: at most nnz / 2048
+  g->tile_cap = g->nnz / 2048 + 1;
+  TC_TRY(dalloc(&g->tile_row, g->tile_cap));
+  TC_TRY(dalloc(&g->tile_cnt, g->tile_cap));
   g->scan.capacity = scan_scratch_entries(n + 1);
   TC_TRY(dalloc(&g->scan.sums, g->scan.capacity));
   return TC_OK;
@@ -111,7 +118,7 @@ tc_status tc_set_params(tc_graph* g, const tc_params* p) {
   if (!g || !p) return TC_ERR_INVALID_ARG;
   const uint32_t c = p->hash_chunk;
   if (c < 32 || c > 16384 || (c & (c - 1)) != 0) return TC_ERR_INVALID_ARG;
-  if (p->edges_per_item == 0 || p->bfs_alpha == 0 || p->bfs_beta == 0) return TC_ERR_INVALID_ARG;
+  if (p->edges_per_item == 0 || p->edges_per_item > 512 || p->bfs_alpha == 0 || p->bfs_beta == 0) return TC_ERR_INVALID_ARG;
   g->params = *p;
   return TC_OK;
 }

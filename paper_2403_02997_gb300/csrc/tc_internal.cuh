@@ -67,6 +67,11 @@ struct tc_graph {
   uint2* cover = nullptr;        // [m]  all cover edges (u < v)
   uint2* large = nullptr;        // [m]  (owner, streamer) of owner-hash cover edges
   uint32_t* ostream = nullptr;   // [m]  streamers bucketed by owner
+  uint32_t* lcol = nullptr;      // [nnz] rows reordered [other-level | same-level] per count
+  unsigned long long* lsplit = nullptr;  // [n] start of the same-level part of each row
+  uint32_t* tile_row = nullptr;  // [tile_cap] row of each tile of a long row (level split)
+  uint32_t* tile_cnt = nullptr;  // [tile_cap] other-level entries per tile
+  unsigned long long tile_cap = 0;
   tc::DevCounters* ctr = nullptr;      // device counters
   tc::DevCounters* ctr_host = nullptr; // pinned mirror
   tc::ScanScratch scan;
