@@ -35,7 +35,9 @@ sys.path.insert(0, ROOT)
 
 from paper_2403_02997_gb300 import gen  # noqa: E402
 
-WORKLOADS = {"rmat24": gen.RMAT_24, "er1024": gen.ER_1024, "mesh4096": gen.MESH_4096}
+WORKLOADS = {"rmat24": gen.RMAT_24, "er1024": gen.ER_1024, "mesh4096": gen.MESH_4096,
+             # smaller cases of the same family, for profiling captures
+             "rmat21": gen.rmat_spec(21, 16, 2), "rmat16": gen.rmat_spec(16, 16, 2)}
 METRIC = "input edges/s (exact triangle count, tc_count on device-resident CSR)"
 L2_BYTES = 129 * 2**20
 
@@ -58,7 +60,7 @@ def parse_args():
 # distributed plumbing (replicas only)
 # ----------------------------------------------------------------------------
 
-def dist_setup(args):
+def dist_setup(args=None):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -411,19 +413,22 @@ def run_ours(args, world, rank, local):
     traffic = profiled_traffic(args.workload)
 
     # end to end through the C ABI from pinned host buffers
-    e2e_steps = max(1, args.e2e_steps)
+    e2e_steps = args.e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(max(e2e_steps, 1) if e2e_steps else 0):
         gh = tc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), spec.n,
                       stream=stream)
         r = gh.max_degree_vertex() if spec.root == "maxdeg" else 0
         c = gh.count(r, stream=stream)
         gh.close()
         assert c == T
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
-    e2e_max = max_over_ranks(t_e2e, world)
-    e2e_value = sum_over_ranks(float(m), world) / e2e_max
+    if e2e_steps:
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
+        e2e_max = max_over_ranks(t_e2e, world)
+        e2e_value = sum_over_ranks(float(m), world) / e2e_max
+    else:  # profiling runs skip the end-to-end leg
+        e2e_max, e2e_value = None, None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
