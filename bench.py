@@ -250,46 +250,51 @@ class OracleSampler:
     """Times the oracle (as it stands) on a bounded sample of the workload.
 
     The graph is built by the oracle (not timed, as tc_graph_create is not in
-    the GPU step).  A sample = the oracle BFS over the whole graph + its full
-    cover-edge scan + the literal CETC-Seq intersection of every stride-th cover
-    edge; the full-graph time is estimated as bfs + scan + (sample - scan) *
-    |S| / intersected.
+    the GPU step).  A sample = the oracle BFS over the whole graph, its full
+    cover-edge scan, and the literal CETC-Seq intersection of a seeded uniform
+    random sample of the cover edges, grown geometrically until it has used
+    about target_s seconds.  The full-graph time is estimated as
+    bfs + scan + (sample time / sampled edges) * |S|.
     """
 
-    def __init__(self, spec, src, dst, root, target_s):
+    def __init__(self, spec, src, dst, root, target_s, seed=11):
         import oracle
         self.o = oracle
         self.rp, self.col = oracle.build_csr(spec.n, src, dst)
         self.m = int(self.col.size // 2)
         self.root = root
-        t = time.perf_counter()
-        self.lv = oracle.bfs_levels(self.rp, self.col, root)
-        self.t_bfs = time.perf_counter() - t
-        t = time.perf_counter()
-        r0 = oracle.cetc(self.rp, self.col, self.lv, stride=1 << 62)
-        self.t_scan = time.perf_counter() - t
-        self.num_cover = r0["num_cover"]
-        s1 = max(1, self.num_cover // 512)
-        t = time.perf_counter()
-        r1 = oracle.cetc(self.rp, self.col, self.lv, stride=s1)
-        t1 = time.perf_counter() - t
-        per_edge = max(t1 - self.t_scan, 1e-9) / max(r1["done"], 1)
-        self.stride = max(1, int(math.ceil(self.num_cover * per_edge / max(target_s, 0.1))))
+        self.target_s = max(float(target_s), 0.5)
+        self.rng = np.random.default_rng(seed)
 
     def step(self) -> dict:
         t = time.perf_counter()
         lv = self.o.bfs_levels(self.rp, self.col, self.root)
         t_bfs = time.perf_counter() - t
         t = time.perf_counter()
-        r = self.o.cetc(self.rp, self.col, lv, stride=self.stride)
-        t_s = time.perf_counter() - t
-        est = t_bfs + self.t_scan + max(t_s - self.t_scan, 0.0) * self.num_cover / max(r["done"], 1)
-        return {"est_seconds": est, "edges": self.m, "done": r["done"], "wall": t_bfs + t_s}
+        cov = self.o.cetc(self.rp, self.col, lv, stride=1 << 62, want_cover=True)
+        t_scan = time.perf_counter() - t
+        S = cov["num_cover"]
+        done, t_sample, k = 0, 0.0, 256
+        while S and t_sample < self.target_s and done < S:
+            k = min(k, S)
+            idx = self.rng.integers(0, S, size=k)
+            t = time.perf_counter()
+            self.o.cetc_edges(self.rp, self.col, lv, cov["cover_u"][idx], cov["cover_v"][idx])
+            dt = time.perf_counter() - t
+            t_sample += dt
+            done += k
+            # grow toward the remaining budget, at most 4x per round
+            k = int(k * min(4.0, max(1.5, (self.target_s - t_sample) / max(dt, 1e-6))))
+        per_edge = t_sample / done if done else 0.0
+        est = t_bfs + t_scan + per_edge * S
+        self.done, self.num_cover = done, S
+        return {"est_seconds": est, "edges": self.m, "done": done,
+                "wall": t_bfs + t_scan + t_sample}
 
     def describe(self, done) -> str:
         return (f"oracle BFS over the whole graph + full cover-edge scan + literal CETC-Seq "
-                f"intersection of 1 in {self.stride} cover edges ({done} of {self.num_cover}), "
-                f"full-graph time scaled from the sample; 1 thread")
+                f"intersection of {done} uniformly sampled cover edges of {self.num_cover}; "
+                f"full-graph time = bfs + scan + per-edge sample time x |S|; 1 thread")
 
 
 # ----------------------------------------------------------------------------

@@ -156,7 +156,9 @@ typedef struct tc_params {
   uint32_t edges_per_item;   /* cover edges per hash work item (1..512) */
   uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
-  uint32_t reserved[3];
+  uint32_t sorted_lookup;    /* 1: look ids up by binary search in the sorted chunk instead of
+                                the cuckoo table (the automatic fallback if a build fails) */
+  uint32_t reserved[2];
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);

@@ -237,6 +237,21 @@ int orc_num_threads(void) {
 }
 
 /*
+ * Algorithm CETC-Seq's count restricted to a given list of k horizontal edges
+ * (us[i] < vs[i]): the sum of their per-edge counts, with the CETC-SM split.
+ * out[0] = T, out[1] = c1, out[2] = c2.  Used to time a sample of the edge
+ * loop; over all of S it equals orc_cetc.
+ */
+void orc_cetc_edges(const int64_t* row_ptr, const uint32_t* col, const int32_t* level,
+                    uint64_t k, const uint32_t* us, const uint32_t* vs, uint64_t* out) {
+  uint64_t t = 0, c1 = 0, c2 = 0;
+  for (uint64_t i = 0; i < k; ++i) t += cover_edge(row_ptr, col, level, us[i], vs[i], &c1, &c2);
+  out[0] = t;
+  out[1] = c1;
+  out[2] = c2;
+}
+
+/*
  * The per-edge count of Algorithm CETC-Seq for one horizontal edge (u, v),
  * u < v: the number of w in N(u) ∩ N(v) with L(u) != L(w), or L(u) == L(w)
  * and v < w.

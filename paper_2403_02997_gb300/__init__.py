@@ -47,7 +47,8 @@ class tc_stats(ctypes.Structure):
 class tc_params(ctypes.Structure):
     _fields_ = [("small_max_degree", ctypes.c_uint32), ("hash_chunk", ctypes.c_uint32),
                 ("edges_per_item", ctypes.c_uint32), ("bfs_alpha", ctypes.c_uint32),
-                ("bfs_beta", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("bfs_beta", ctypes.c_uint32), ("sorted_lookup", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 _lib = None

@@ -395,16 +395,23 @@ __device__ __forceinline__ void load_block(const uint32_t* __restrict__ arr, uns
   }
 }
 
-// The warp streams arr[cur, end) up to the first id above hi (when bounded),
-// looking every element up in the chunk; returns the new cursor.  A hit counts
-// to c1 for a segment of other-level neighbours (kSame = false) and to c2' for
-// the same-level neighbours above v (kSame = true).  The next block of
+// Lookup of one streamed id in the chunk: the cuckoo table, or for a chunk
+// whose table could not be built, the sorted copy.
+template <bool kSorted>
+__device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_len, uint32_t w) {
+  if (kSorted) return sorted_contains(ck.table, sorted_len, w);
+  return ck.contains(w);
+}
+
+// The warp streams arr[cur, end) up to the first id above hi (kBounded; the
+// last chunk of a row is unbounded), looking every element up in the chunk;
+// returns the new cursor and adds the hits.  The next block of
 // kStreamUnroll x 32 elements is loaded before the current one is looked up.
-template <bool kSame>
+// Unbounded full blocks skip the end test.
+template <bool kBounded, bool kSorted>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, unsigned long long cur, const unsigned long long end,
-    const bool bounded, const uint32_t hi, const Cuckoo& ck, const bool sorted,
-    const uint32_t sorted_len, uint32_t& hits) {
+    const uint32_t hi, const Cuckoo& ck, const uint32_t sorted_len, uint32_t& hits) {
   if (cur >= end) return end;
   const unsigned lane = lane_id();
   uint32_t w[kStreamUnroll];
@@ -414,22 +421,49 @@ __device__ __forceinline__ unsigned long long stream_segment(
     const bool more = next < end;
     uint32_t wn[kStreamUnroll];
     if (more) load_block(arr, next, end, wn);
-    const unsigned long long left = end - cur;
-    const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
+    if (!kBounded && more) {
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
-      const uint32_t j = lane + 32u * u;
-      const bool in = j < rem && (!bounded || w[u] <= hi);
-      const unsigned stop = __ballot_sync(0xffffffffu, !in);
-      const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
-      if (lane < take) hits += sorted ? sorted_contains(ck.table, sorted_len, w[u]) : ck.contains(w[u]);
-      if (stop) return cur + 32ull * u + take;
+      for (int u = 0; u < kStreamUnroll; ++u) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
+    } else {
+      const unsigned long long left = end - cur;
+      const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
+#pragma unroll
+      for (int u = 0; u < kStreamUnroll; ++u) {
+        const uint32_t j = lane + 32u * u;
+        const bool in = j < rem && (!kBounded || w[u] <= hi);
+        const unsigned stop = __ballot_sync(0xffffffffu, !in);
+        const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
+        if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
+        if (stop) return cur + 32ull * u + take;
+      }
     }
     if (!more) return end;
     cur = next;
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) w[u] = wn[u];
   }
+}
+
+// Both segments of one cover edge for one chunk; returns the new cursors.
+template <bool kBounded, bool kSorted>
+__device__ __forceinline__ void stream_edge(const uint32_t* __restrict__ lcol,
+                                            unsigned long long& a, unsigned long long ae,
+                                            unsigned long long& b, unsigned long long be,
+                                            uint32_t hi, const Cuckoo& ck, uint32_t sorted_len,
+                                            uint32_t& c1, uint32_t& c2c) {
+  a = stream_segment<kBounded, kSorted>(lcol, a, ae, hi, ck, sorted_len, c1);
+  b = stream_segment<kBounded, kSorted>(lcol, b, be, hi, ck, sorted_len, c2c);
+}
+
+// The rare path (a chunk kept as a sorted array), out of line so it does not
+// weigh on the registers of the hot loop.
+__device__ __noinline__ void stream_edge_sorted(const uint32_t* __restrict__ lcol,
+                                                unsigned long long& a, unsigned long long ae,
+                                                unsigned long long& b, unsigned long long be,
+                                                bool bounded, uint32_t hi, const Cuckoo& ck,
+                                                uint32_t sorted_len, uint32_t& c1, uint32_t& c2c) {
+  if (bounded) stream_edge<true, true>(lcol, a, ae, b, be, hi, ck, sorted_len, c1, c2c);
+  else stream_edge<false, true>(lcol, a, ae, b, be, hi, ck, sorted_len, c1, c2c);
 }
 
 // First index in arr[a, b) (sorted) with arr[i] >= t.
@@ -455,7 +489,8 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     const uint32_t* __restrict__ lcol, const unsigned long long* __restrict__ lsplit,
     const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
     const unsigned long long* __restrict__ ioff, const uint32_t* __restrict__ item_owner,
-    unsigned long long nitems, uint32_t chunk, uint32_t per_item, DevCounters* ctr) {
+    unsigned long long nitems, uint32_t chunk, uint32_t per_item, uint32_t force_sorted,
+    DevCounters* ctr) {
   extern __shared__ uint4 table4[];
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
@@ -500,11 +535,12 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
       for (uint32_t i = threadIdx.x; i < (1u << (fbits - 5)); i += blockDim.x) filter[i] = 0u;
       if (threadIdx.x == 0) {
         s_next = 0;
-        s_fail = 0;
+        s_fail = force_sorted;
       }
       __syncthreads();
-      for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x)
-        if (!ck.insert(col[j], threadIdx.x)) s_fail = 1;
+      if (!force_sorted)
+        for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x)
+          if (!ck.insert(col[j], threadIdx.x)) s_fail = 1;
       __syncthreads();
       const bool sorted = s_fail != 0;
       if (sorted) {  // rare: keep the chunk as a sorted array instead
@@ -517,10 +553,14 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= ne) break;
         uint32_t c1 = 0, c2c = 0;
-        const unsigned long long a =
-            stream_segment<false>(lcol, s_a[i], s_ae[i], bounded, hi_id, ck, sorted, entries, c1);
-        const unsigned long long b =
-            stream_segment<true>(lcol, s_b[i], s_be[i], bounded, hi_id, ck, sorted, entries, c2c);
+        unsigned long long a = s_a[i], b = s_b[i];
+        const unsigned long long ae = s_ae[i], be = s_be[i];
+        if (!sorted) {
+          if (bounded) stream_edge<true, false>(lcol, a, ae, b, be, hi_id, ck, entries, c1, c2c);
+          else stream_edge<false, false>(lcol, a, ae, b, be, hi_id, ck, entries, c1, c2c);
+        } else {
+          stream_edge_sorted(lcol, a, ae, b, be, bounded, hi_id, ck, entries, c1, c2c);
+        }
         if (lane == 0) {
           s_a[i] = a;
           s_b[i] = b;
@@ -610,7 +650,8 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
   k_owner_hash<<<grid, kHashBlock, smem, st>>>(g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff,
                                               g->ostream, g->ioff, g->item_owner, nitems, chunk,
-                                              per_item, g->ctr); TC_LAUNCHED();
+                                              per_item, g->params.sorted_lookup ? 1u : 0u,
+                                              g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

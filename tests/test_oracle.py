@@ -283,6 +283,19 @@ def test_levels_match_networkx_with_restarts():
         assert np.array_equal(L.astype(np.int64), expect)
 
 
+def test_edge_list_count_equals_full_loop():
+    n = 1 << 11
+    s, d = gen.rmat_edges(11, 8, 5)
+    rp, col = oracle.build_csr(n, s, d)
+    lv = oracle.bfs_levels(rp, col, 3)
+    full = oracle.cetc(rp, col, lv, want_cover=True)
+    part = oracle.cetc_edges(rp, col, lv, full["cover_u"], full["cover_v"])
+    assert (part["T"], part["c1"], part["c2"]) == (full["T"], full["c1"], full["c2"])
+    half = oracle.cetc_edges(rp, col, lv, full["cover_u"][::2], full["cover_v"][::2])
+    other = oracle.cetc_edges(rp, col, lv, full["cover_u"][1::2], full["cover_v"][1::2])
+    assert half["T"] + other["T"] == full["T"]
+
+
 def test_root_invariance_and_sampling():
     n = 1 << 10
     s, d = gen.rmat_edges(10, 8, 77)
