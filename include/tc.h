@@ -164,6 +164,37 @@ typedef struct tc_params {
 tc_status tc_params_default(tc_params* p);
 tc_status tc_set_params(tc_graph* g, const tc_params* p);
 
+/*
+ * BFS levels of a caller-owned device graph, allocating no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- applications that own all device memory through their own
+ * pool or a fixed budget, and services that must not allocate once running.
+ *
+ * row_ptr (device, n+1 uint64 offsets) and col (device, row_ptr[n] uint32 ids)
+ * are an undirected graph in CSR form: every edge in both rows, no self-loops;
+ * rows need not be sorted (tc_get_csr's output qualifies).  levels (device, n
+ * int32) receives L(v): the BFS distance from root, and for vertices the root
+ * does not reach, the distance from the smallest id of their component (the
+ * restart rule of Algorithm CETC-Seq), so every entry ends >= 0.  The caller
+ * owns all three arrays; nothing is retained after the call returns.  Work is
+ * ordered on `stream`, which the call synchronises once per BFS level.
+ *
+ * Scratch: one fixed __device__ array of 12 MiB + 256 B (queues and union-find
+ * parents for up to 2^20 vertices), held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up its address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * leaves its contents behind; the call clears what it needs.  Calls whose
+ * device work overlaps (other streams or host threads at the same time) race
+ * on the shared array: serialise them.
+ *
+ * Errors: TC_ERR_OVERFLOW if n > 2^20 (nothing is written); TC_ERR_INVALID_ARG
+ * for a NULL pointer or root >= n; TC_ERR_CUDA.  n == 0 returns TC_OK at once.
+ */
+tc_status tc_bfs_levels_noalloc(const uint64_t* row_ptr, const uint32_t* col, uint32_t n,
+                                uint32_t root, int32_t* levels, void* stream);
+
 /* Human-readable name of a status. */
 const char* tc_status_string(tc_status s);
 

@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "tc_params_default": ([P(tc_params)], ctypes.c_int),
         "tc_set_params": ([vp, P(tc_params)], ctypes.c_int),
         "tc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "tc_bfs_levels_noalloc": ([vp, vp, u32, u32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +219,18 @@ def tc_set_params(handle: int, **kw) -> None:
     for k, v in kw.items():
         setattr(p, k, int(v))
     _check(lib.tc_set_params(handle, ctypes.byref(p)), "tc_set_params")
+
+
+def tc_bfs_levels_noalloc(row_ptr, col, n: int, root: int, levels, stream=None) -> None:
+    """BFS levels of a device CSR into a device int32 array, allocating nothing.
+
+    row_ptr (uint64 / int64, n+1), col (uint32 / int32) and levels (int32, n)
+    are CUDA tensors owned by the caller; see include/tc.h for the limits
+    (n <= 2^20) and the shared-scratch rules.
+    """
+    _check(load_library().tc_bfs_levels_noalloc(row_ptr.data_ptr(), col.data_ptr(), n, root,
+                                                levels.data_ptr(), _stream_handle(stream)),
+           "tc_bfs_levels_noalloc")
 
 
 # ----------------------------------------------------------------------------
