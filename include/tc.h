@@ -158,7 +158,13 @@ typedef struct tc_params {
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
   uint32_t sorted_lookup;    /* 1: look ids up by binary search in the sorted chunk instead of
                                 the cuckoo table (the automatic fallback if a build fails) */
-  uint32_t reserved[2];
+  uint32_t persistent_bfs;   /* 1 (default): runs of small frontiers go to one persistent
+                                cooperative kernel with a device-side grid barrier */
+  uint32_t barrier_timeout_ms; /* bound on each device-side barrier wait (default 2000); past it
+                                  the count fails with TC_ERR_TIMEOUT and the handle stays usable */
+  uint32_t test_barrier_skip;  /* testing only: 1 makes one block leave the persistent kernel
+                                  without arriving at a barrier, so the other blocks time out */
+  uint32_t reserved[3];
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);

@@ -48,7 +48,8 @@ class tc_params(ctypes.Structure):
     _fields_ = [("small_max_degree", ctypes.c_uint32), ("hash_chunk", ctypes.c_uint32),
                 ("edges_per_item", ctypes.c_uint32), ("bfs_alpha", ctypes.c_uint32),
                 ("bfs_beta", ctypes.c_uint32), ("sorted_lookup", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("persistent_bfs", ctypes.c_uint32), ("barrier_timeout_ms", ctypes.c_uint32),
+                ("test_barrier_skip", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 _lib = None

@@ -11,6 +11,14 @@
 //                         vertex, early exit) for a neighbour at level l.
 //   Switch to bottom-up when the frontier's edges exceed the unexplored edges
 //   / alpha; back to top-down when the frontier falls below n / beta.
+// Small frontiers (long, thin graphs such as meshes and road networks, and the
+//   tails of every search) run in one persistent cooperative kernel,
+//   k_bfs_persistent: one block per SM, one warp per frontier vertex, and a
+//   device-side grid barrier between levels, until the frontier empties or
+//   grows past kPersistMaxVerts / kPersistMaxEdges.  Every barrier wait is
+//   bounded by barrier_timeout_ms (%globaltimer); past it the kernel records
+//   kErrTimeout and every block leaves, so a count fails with TC_ERR_TIMEOUT
+//   instead of hanging.
 // Restart phase: the vertices left unvisited form whole components.  Their
 //   components are found by union-find that always hooks the larger root under
 //   the smaller, so each root is its component's smallest id — exactly the
@@ -27,6 +35,10 @@ constexpr int kTdBlock = 256;
 constexpr int kTdEdgesPerBlock = 2048;
 constexpr int kBuBlock = 256;
 constexpr int kBuGroup = 8;
+
+constexpr int kPersistBlock = 512;
+constexpr unsigned long long kPersistMaxVerts = 1ull << 16;
+constexpr unsigned long long kPersistMaxEdges = 1ull << 19;
 
 __global__ void k_set_root(int32_t* level, uint32_t* queue, uint32_t root) {
   level[root] = 0;
@@ -152,6 +164,114 @@ __global__ void k_count_unvisited(const int32_t* __restrict__ level, uint32_t n,
   if (lane_id() == 0 && c) atomicAdd(&ctr->unvisited, c);
 }
 
+// ---- persistent search for small frontiers --------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a co-resident grid (cooperative launch).  The last
+// block to arrive resets the count and advances the generation; the others
+// wait for the generation to change, each for at most budget_ns, and give up
+// (recording kErrTimeout) when the budget runs out or another block already
+// gave up.  Returns false, to every thread of the block, when it gave up.
+__device__ bool grid_barrier(DevCounters* c, unsigned nblocks, unsigned long long budget_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* genp = &c->bar_gen;
+    volatile unsigned int* errp = &c->err;
+    const unsigned int gen = *genp;
+    __threadfence();
+    if (atomicAdd(&c->bar_count, 1u) == nblocks - 1) {
+      atomicExch(&c->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*genp == gen) {
+        if ((*errp & kErrTimeout) || global_ns() - t0 > budget_ns) {
+          atomicOr(&c->err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void k_persist_init(DevCounters* c, unsigned long long qlen) {
+  c->plen[0] = qlen;
+  c->plen[1] = c->plen[2] = 0;
+  c->pedges[0] = c->pedges[1] = c->pedges[2] = 0;
+  c->bar_count = 0;
+}
+
+// Levels lvl0, lvl0+1, ... top-down from the frontier in q0 (its length in
+// plen[0]).  Iteration it reads the frontier of slot it%3 from queue it&1 and
+// appends the next one to slot (it+1)%3 / queue (it+1)&1; block 0 clears slot
+// (it+2)%3, which every block finished reading before the previous barrier.
+// Queues and slot counters written by other blocks are read with __ldcg (L2),
+// never through a stale L1 line.
+__global__ void __launch_bounds__(kPersistBlock) k_bfs_persistent(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    int32_t* level, uint32_t* q0, uint32_t* q1, int32_t lvl0, unsigned long long budget_ns,
+    int test_skip, DevCounters* c) {
+  const unsigned lane = lane_id();
+  const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * blockDim.x / 32;
+  int32_t lvl = lvl0;
+  for (unsigned it = 0;; ++it) {
+    const unsigned cur = it % 3, nxt = (it + 1) % 3, old = (it + 2) % 3;
+    const uint32_t* q = (it & 1) ? q1 : q0;
+    uint32_t* nq = (it & 1) ? q0 : q1;
+    const unsigned long long qlen = __ldcg(&c->plen[cur]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->plen[old] = 0;
+      c->pedges[old] = 0;
+    }
+    for (unsigned long long i = gwarp; i < qlen; i += nwarps) {
+      const uint32_t u = __ldcg(q + i);
+      const unsigned long long b = row_ptr[u], e = row_ptr[u + 1];
+      for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+        const unsigned long long j = j0 + lane;
+        bool take = false;
+        uint32_t w = 0;
+        unsigned long long deg = 0;
+        if (j < e) {
+          w = col[j];
+          if (__ldcg(level + w) == -1) take = atomicCAS(&level[w], -1, lvl + 1) == -1;
+          if (take) deg = row_ptr[w + 1] - row_ptr[w];
+        }
+        warp_append(take, w, nq, &c->plen[nxt]);
+        deg = warp_sum(deg);
+        if (lane == 0 && deg) atomicAdd(&c->pedges[nxt], deg);
+      }
+    }
+    if (test_skip && blockIdx.x == 0) return;  // testing: this block never arrives
+    if (!grid_barrier(c, gridDim.x, budget_ns)) return;
+    const unsigned long long nlen = __ldcg(&c->plen[nxt]);
+    const unsigned long long nedges = __ldcg(&c->pedges[nxt]);
+    ++lvl;
+    if (nlen == 0 || nlen > kPersistMaxVerts || nedges > kPersistMaxEdges) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->p_level = (unsigned)lvl;
+        c->p_slot = nxt;
+        c->p_buf = (it + 1) & 1;
+      }
+      return;
+    }
+  }
+}
+
 // ---- restart components -------------------------------------------------
 
 __global__ void k_cc_init(uint32_t* parent, uint32_t n) {
@@ -224,6 +344,40 @@ tc_status reset_next(tc_graph* g, cudaStream_t st) {
   return TC_OK;
 }
 
+// One persistent run from the frontier q (qlen vertices at level lvl).  On
+// return the search has advanced to *next_lvl, whose frontier (*next_len
+// vertices, possibly none) is in nq when *next_in_b, else in q.
+tc_status run_persistent(tc_graph* g, uint32_t* q, uint32_t* nq, uint64_t qlen, int32_t lvl,
+                         cudaStream_t st, int32_t* next_lvl, uint64_t* next_len, bool* next_in_b) {
+  static int coop = -1, per_sm = 0;
+  if (coop < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, kPersistBlock, 0);
+  }
+  if (!coop || per_sm < 1) return TC_ERR_CUDA;
+  k_persist_init<<<1, 1, 0, st>>>(g->ctr, qlen); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  const unsigned long long budget_ns = 1000000ull * g->params.barrier_timeout_ms;
+  int test_skip = g->params.test_barrier_skip ? 1 : 0;
+  const unsigned long long* rp = g->row_ptr;
+  const uint32_t* cl = g->col;
+  int32_t* lv = g->level;
+  DevCounters* c = g->ctr;
+  void* args[] = {(void*)&rp, (void*)&cl, (void*)&lv, (void*)&q, (void*)&nq, (void*)&lvl,
+                  (void*)&budget_ns, (void*)&test_skip, (void*)&c};
+  TC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bfs_persistent, dim3(num_sms()),
+                                          dim3(kPersistBlock), args, 0, st)); TC_LAUNCHED();
+  TC_TRY(read_counters(g, st));
+  const DevCounters& h = *g->ctr_host;
+  if (h.err & kErrTimeout) return TC_ERR_TIMEOUT;
+  *next_lvl = (int32_t)h.p_level;
+  *next_len = h.plen[h.p_slot];
+  *next_in_b = h.p_buf == 1;
+  return TC_OK;
+}
+
 // Level-synchronous search from the vertices already in queue_a (qlen of them,
 // all at level 0).  Returns the number of levels (1 + deepest level).
 tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* levels_out) {
@@ -249,6 +403,28 @@ tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* leve
       TC_CUDA_TRY(cudaStreamSynchronize(st));
       fedges = g->ctr_host->scan_total;
       if ((long double)fedges * alpha > unexplored && qlen > 1) bottom_up = true;
+      if (!bottom_up && g->params.persistent_bfs && qlen <= kPersistMaxVerts &&
+          fedges <= kPersistMaxEdges && fedges > 0) {
+        int32_t next_lvl = lvl;
+        uint64_t next_len = 0;
+        bool next_in_b = false;
+        TC_TRY(run_persistent(g, q, nq, qlen, lvl, st, &next_lvl, &next_len, &next_in_b));
+        g->stats.bfs_steps += (uint32_t)(next_lvl - lvl);
+        unexplored -= (long double)fedges;  // the first step's edges; later ones are small
+        prev_frontier = next_len;
+        if (next_in_b) {
+          uint32_t* t = q;
+          q = nq;
+          nq = t;
+        }
+        qlen = next_len;
+        if (qlen == 0) {
+          lvl = next_lvl - 1;
+          break;
+        }
+        lvl = next_lvl;
+        continue;
+      }
     }
     TC_TRY(reset_next(g, st));
     uint64_t found;
@@ -297,6 +473,7 @@ tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st) {
   g->stats.bfs_steps = 0;
   g->stats.bottom_up_steps = 0;
   g->stats.restarted = 0;
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
   TC_CUDA_TRY(cudaMemsetAsync(g->level, 0xFF, sizeof(int32_t) * n, st));
   k_set_root<<<1, 1, 0, st>>>(g->level, g->queue_a, root); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());

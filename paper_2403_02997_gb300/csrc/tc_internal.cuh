@@ -27,6 +27,13 @@ struct DevCounters {
   unsigned long long items;      // owner-hash work items
   unsigned long long item_cursor;// dynamic work counter
   unsigned long long unvisited;  // vertices still unvisited
+  unsigned long long plen[3];    // persistent BFS: frontier lengths, one slot per level mod 3
+  unsigned long long pedges[3];  // persistent BFS: degree sums of those frontiers
+  unsigned int bar_count;        // grid barrier: blocks arrived
+  unsigned int bar_gen;          // grid barrier: generation
+  unsigned int p_level;          // persistent BFS: level of the frontier it stopped at
+  unsigned int p_slot;           // ... its length slot
+  unsigned int p_buf;            // ... which queue holds it (0: first, 1: second)
   unsigned int err;              // kErr* flags
   unsigned int dmax;             // largest degree
   unsigned int dmax_vertex;      // smallest id of largest degree
