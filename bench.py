@@ -48,7 +48,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="rmat24")
+    p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle intersection work in the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -225,7 +226,7 @@ def hash_kernel_bytes(rp, col, level, cu, cv, params) -> dict:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ["count.cu", "tc_internal.cuh"]:
+    for f in ["count.cu"]:
         h.update(open(os.path.join(ROOT, "paper_2403_02997_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -481,12 +482,111 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_batched(args, world, rank, local):
+    """The batched workload: graphs of uneven size counted together.
+
+    value = graphs counted per second by tc_batch_count on device-resident
+    graphs (whole job over ranks); beside it, the same graphs counted one
+    tc_count at a time on the same GPU, and tc_count_many end to end from host
+    edge lists (graph builds included).
+    """
+    import torch
+    import paper_2403_02997_gb300 as tc
+    from paper_2403_02997_gb300 import build as tcbuild
+    tcbuild.build_all()
+    torch.cuda.set_device(local)
+    specs = gen.batched_specs(args.batch_graphs, master_seed=4 + 1000 * rank)
+    edges = [sp.edges() for sp in specs]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    gs = [tc.Graph(s, d, sp.n, stream=stream) for sp, (s, d) in zip(specs, edges)]
+    t_create = time.perf_counter() - t0
+    roots = [g.max_degree_vertex() if sp.root == "maxdeg" else 0 for g, sp in zip(gs, specs)]
+    m_total = sum(g.m for g in gs)
+    b = tc.Batch(gs, stream=stream)
+    counts = None
+    for _ in range(args.warmup):
+        counts = b.count(roots, stream=stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        c = b.count(roots, stream=stream)
+        assert counts is None or c == counts
+        counts = c
+    ev1.record(stream)
+    stream.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    st = b.stats()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    graphs_total = sum_over_ranks(float(len(gs)) * args.steps, world)
+    value = graphs_total / (ms / 1e3)
+    # one tc_count per graph, same GPU, same graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = [g.count(r, stream=stream) for g, r in zip(gs, roots)]
+    t_single = time.perf_counter() - t0
+    assert single == counts
+    b.close()
+    # end to end: host edge lists -> graphs -> one batched count -> host counts
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = [tc.Graph(s, d, sp.n, stream=stream) for sp, (s, d) in zip(specs, edges)]
+    e2e_counts = tc.count_many(hs, roots, stream=stream)
+    for h in hs:
+        h.close()
+    t_e2e = time.perf_counter() - t0
+    assert e2e_counts == counts
+    for g in gs:
+        g.close()
+    if rank != 0:
+        return 0
+    h2d = sum(8 * int(s.size) for s, _ in edges)
+    line = {
+        "metric": f"graphs/s (batched count of {len(gs)} graphs, device-resident)",
+        "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": "batched", "graphs": len(gs), "n_log_uniform": [64, 65536],
+                   "families": "even: ER mean degree U[4,64]; odd: R-MAT ef U{8..16}",
+                   "master_seed": 4, "vertices": int(sum(sp.n for sp in specs)),
+                   "edges_undirected": int(m_total), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2"},
+        "edges_per_s": sum_over_ranks(float(m_total) * args.steps, world) / (ms / 1e3),
+        "one_count_per_graph": {"graphs_per_s": len(gs) / t_single, "seconds": t_single},
+        "speedup_vs_one_count_per_graph": (len(gs) / (ms / 1e3 / args.steps)) / (len(gs) / t_single),
+        "triangles_total": int(sum(counts)),
+        "phase_ms": {"bfs": st["ms_bfs"], "cover": st["ms_cover"],
+                     "intersect": st["ms_intersect"], "owner_hash": st["ms_hash"]},
+        "graph_build_seconds": t_create,
+        "e2e": {"value": len(gs) / t_e2e, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8 * len(gs), "seconds_per_step": t_e2e,
+                "what": "tc_graph_create from host edge lists for every graph + tc_count_many"},
+        "gpu_launches": st["launches"] * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
+            if args.workload == "batched":
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the batched workload is timed for the GPU arm only"}))
+                return 0
             return run_reference(args, world, rank)
+        if args.workload == "batched":
+            return run_batched(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

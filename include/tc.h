@@ -92,18 +92,24 @@ tc_status tc_graph_info(const tc_graph* g, uint32_t* n, uint64_t* m, uint32_t* d
 tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count);
 
 /*
- * Count k graphs (roots[i] for gs[i]) in batched launches on `stream`:
- * graphs run concurrently in shared persistent kernels over a table of
- * per-graph device offsets.  counts (host, k entries) receives one count per
- * graph, equal to what tc_count gives for that graph and root.  gs[i] must be
- * pairwise distinct.  Errors as tc_count; on error no count is written.
+ * Count k graphs (roots[i] for gs[i]) together (the batched form of the
+ * data-parallel Algorithm CETC-SM): the graphs are concatenated into one CSR
+ * with per-graph vertex and entry offsets, and every phase runs as one sequence
+ * of launches over all of them -- a multi-source BFS from the k roots, one
+ * cover-edge pass, one owner-hash pass -- with each hit added to its graph's
+ * counter.  counts (host, k entries) receives one count per graph, equal to
+ * what tc_count gives for that graph and root.  gs[i] must be pairwise
+ * distinct; the tunables are those of gs[0].  Builds a temporary batch (see
+ * tc_batch_create) and frees it before returning.  Errors as tc_count and
+ * tc_batch_create; on error no count is written.
  */
 tc_status tc_count_many(tc_graph* const* gs, const uint32_t* roots, size_t k, void* stream,
                         uint64_t* counts);
 
 /*
- * Introspection of the last tc_count / tc_count_many on this handle, for
- * parity checks.  Each call synchronises the device work of that count.
+ * Introspection of the last tc_count on this handle, for parity checks (a
+ * batched count reports through tc_batch_get_*).  Each call synchronises the
+ * device.
  */
 
 /* host_levels[n] receives L(v) (int32, every vertex >= 0 after a count). */
@@ -169,6 +175,25 @@ typedef struct tc_params {
 
 tc_status tc_params_default(tc_params* p);
 tc_status tc_set_params(tc_graph* g, const tc_params* p);
+
+/*
+ * A reusable batch of graphs (for repeated counts, e.g. a serving loop).
+ * tc_batch_create copies the k graphs' CSRs into one concatenated device CSR
+ * (the handles stay owned by the caller and may be destroyed afterwards) and
+ * sizes the per-count state for the union.  Errors: TC_ERR_INVALID_ARG (k == 0,
+ * NULL or repeated handles), TC_ERR_OVERFLOW (more than 2^31 - 1 vertices in
+ * total), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+typedef struct tc_batch tc_batch;
+tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch** out);
+/* roots[i] < n_i of graph i (ignored for empty graphs); counts: host, k entries. */
+tc_status tc_batch_count(tc_batch* b, const uint32_t* roots, void* stream, uint64_t* counts);
+tc_status tc_batch_set_params(tc_batch* b, const tc_params* p);
+/* Statistics of the last tc_batch_count, summed over the batch. */
+tc_status tc_batch_get_stats(const tc_batch* b, tc_stats* out);
+/* Levels of graph i after tc_batch_count: host_levels[n_i]. */
+tc_status tc_batch_get_levels(const tc_batch* b, size_t i, int32_t* host_levels);
+tc_status tc_batch_destroy(tc_batch* b);
 
 /*
  * BFS levels of a caller-owned device graph, allocating no device memory.

@@ -81,6 +81,12 @@ def load_library(path: str = LIB_PATH):
         "tc_set_params": ([vp, P(tc_params)], ctypes.c_int),
         "tc_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "tc_bfs_levels_noalloc": ([vp, vp, u32, u32, vp, vp], ctypes.c_int),
+        "tc_batch_create": ([P(vp), ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
+        "tc_batch_count": ([vp, P(u32), vp, P(u64)], ctypes.c_int),
+        "tc_batch_set_params": ([vp, P(tc_params)], ctypes.c_int),
+        "tc_batch_get_stats": ([vp, P(tc_stats)], ctypes.c_int),
+        "tc_batch_get_levels": ([vp, ctypes.c_size_t, vp], ctypes.c_int),
+        "tc_batch_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -288,3 +294,55 @@ class Graph:
 
 def count_many(graphs: Sequence[Graph], roots: Sequence[int], stream=None) -> list:
     return tc_count_many([g.handle for g in graphs], roots, stream)
+
+
+class Batch:
+    """A reusable batch: the graphs' CSRs concatenated once, counted together."""
+
+    def __init__(self, graphs: Sequence[Graph], stream=None):
+        lib = load_library()
+        self.k = len(graphs)
+        self.sizes = [g.n for g in graphs]
+        hs = (ctypes.c_void_p * self.k)(*[g.handle for g in graphs])
+        out = ctypes.c_void_p()
+        _check(lib.tc_batch_create(hs, self.k, _stream_handle(stream), ctypes.byref(out)),
+               "tc_batch_create")
+        self.handle = out.value
+
+    def count(self, roots: Sequence[int], stream=None) -> list:
+        rs = (ctypes.c_uint32 * self.k)(*roots)
+        out = (ctypes.c_uint64 * self.k)()
+        _check(load_library().tc_batch_count(self.handle, rs, _stream_handle(stream), out),
+               "tc_batch_count")
+        return [int(x) for x in out]
+
+    def set_params(self, **kw) -> None:
+        p = tc_params()
+        lib = load_library()
+        _check(lib.tc_params_default(ctypes.byref(p)), "tc_params_default")
+        for k_, v in kw.items():
+            setattr(p, k_, int(v))
+        _check(lib.tc_batch_set_params(self.handle, ctypes.byref(p)), "tc_batch_set_params")
+
+    def stats(self) -> dict:
+        s = tc_stats()
+        _check(load_library().tc_batch_get_stats(self.handle, ctypes.byref(s)), "tc_batch_get_stats")
+        return {name: getattr(s, name) for name, _ in tc_stats._fields_}
+
+    def levels(self, i: int) -> np.ndarray:
+        out = np.empty(self.sizes[i], dtype=np.int32)
+        _check(load_library().tc_batch_get_levels(self.handle, i,
+                                                  out.ctypes.data if out.size else None),
+               "tc_batch_get_levels")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _check(load_library().tc_batch_destroy(self.handle), "tc_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -39,6 +39,7 @@ constexpr int kBuGroup = 8;
 constexpr int kPersistBlock = 512;
 constexpr unsigned long long kPersistMaxVerts = 1ull << 16;
 constexpr unsigned long long kPersistMaxEdges = 1ull << 19;
+constexpr unsigned int kPersistMaxDeg = 4096;  // one warp expands a vertex in the persistent kernel
 
 __global__ void k_set_root(int32_t* level, uint32_t* queue, uint32_t root) {
   level[root] = 0;
@@ -47,12 +48,17 @@ __global__ void k_set_root(int32_t* level, uint32_t* queue, uint32_t root) {
 
 __global__ void k_frontier_degrees(const uint32_t* __restrict__ queue, uint64_t qlen,
                                    const unsigned long long* __restrict__ row_ptr,
-                                   uint32_t* __restrict__ fdeg) {
+                                   uint32_t* __restrict__ fdeg, unsigned int* fmaxdeg) {
+  unsigned int mx = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < qlen;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t u = queue[i];
-    fdeg[i] = (uint32_t)(row_ptr[u + 1] - row_ptr[u]);
+    const uint32_t d = (uint32_t)(row_ptr[u + 1] - row_ptr[u]);
+    fdeg[i] = d;
+    mx = d > mx ? d : mx;
   }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane_id() == 0 && mx) atomicMax(fmaxdeg, mx);
 }
 
 // Largest i in [lo, hi] with qoff[i] <= e (qoff nondecreasing, qoff[lo] <= e).
@@ -212,6 +218,7 @@ __global__ void k_persist_init(DevCounters* c, unsigned long long qlen) {
   c->plen[0] = qlen;
   c->plen[1] = c->plen[2] = 0;
   c->pedges[0] = c->pedges[1] = c->pedges[2] = 0;
+  c->pmaxdeg[0] = c->pmaxdeg[1] = c->pmaxdeg[2] = 0;
   c->bar_count = 0;
 }
 
@@ -237,6 +244,7 @@ __global__ void __launch_bounds__(kPersistBlock) k_bfs_persistent(
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       c->plen[old] = 0;
       c->pedges[old] = 0;
+      c->pmaxdeg[old] = 0;
     }
     for (unsigned long long i = gwarp; i < qlen; i += nwarps) {
       const uint32_t u = __ldcg(q + i);
@@ -252,16 +260,22 @@ __global__ void __launch_bounds__(kPersistBlock) k_bfs_persistent(
           if (take) deg = row_ptr[w + 1] - row_ptr[w];
         }
         warp_append(take, w, nq, &c->plen[nxt]);
+        const unsigned int dmax = __reduce_max_sync(0xffffffffu, (unsigned int)deg);
         deg = warp_sum(deg);
-        if (lane == 0 && deg) atomicAdd(&c->pedges[nxt], deg);
+        if (lane == 0 && deg) {
+          atomicAdd(&c->pedges[nxt], deg);
+          atomicMax(&c->pmaxdeg[nxt], dmax);
+        }
       }
     }
     if (test_skip && blockIdx.x == 0) return;  // testing: this block never arrives
     if (!grid_barrier(c, gridDim.x, budget_ns)) return;
     const unsigned long long nlen = __ldcg(&c->plen[nxt]);
     const unsigned long long nedges = __ldcg(&c->pedges[nxt]);
+    const unsigned int nmax = __ldcg(&c->pmaxdeg[nxt]);
     ++lvl;
-    if (nlen == 0 || nlen > kPersistMaxVerts || nedges > kPersistMaxEdges) {
+    if (nlen == 0 || nlen > kPersistMaxVerts || nedges > kPersistMaxEdges ||
+        nmax > kPersistMaxDeg) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->p_level = (unsigned)lvl;
         c->p_slot = nxt;
@@ -395,16 +409,20 @@ tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* leve
     unsigned long long fedges = 0;
     if (!bottom_up) {
       if (qlen == 0) break;
-      k_frontier_degrees<<<grid_for(qlen, 256, sms * 16), 256, 0, st>>>(q, qlen, g->row_ptr, g->fdeg); TC_LAUNCHED();
+      TC_CUDA_TRY(cudaMemsetAsync(&g->ctr->fmaxdeg, 0, sizeof(unsigned int), st));
+      k_frontier_degrees<<<grid_for(qlen, 256, sms * 16), 256, 0, st>>>(q, qlen, g->row_ptr, g->fdeg,
+                                                                        &g->ctr->fmaxdeg); TC_LAUNCHED();
       TC_CUDA_TRY(cudaGetLastError());
       TC_TRY(exclusive_scan_u32(g->fdeg, g->qoff, qlen, g->scan, st));
       TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr_host->scan_total, g->qoff + qlen, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st));
+      TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr_host->fmaxdeg, &g->ctr->fmaxdeg, sizeof(unsigned int),
                                   cudaMemcpyDeviceToHost, st));
       TC_CUDA_TRY(cudaStreamSynchronize(st));
       fedges = g->ctr_host->scan_total;
       if ((long double)fedges * alpha > unexplored && qlen > 1) bottom_up = true;
       if (!bottom_up && g->params.persistent_bfs && qlen <= kPersistMaxVerts &&
-          fedges <= kPersistMaxEdges && fedges > 0) {
+          fedges <= kPersistMaxEdges && fedges > 0 && g->ctr_host->fmaxdeg <= kPersistMaxDeg) {
         int32_t next_lvl = lvl;
         uint64_t next_len = 0;
         bool next_in_b = false;
@@ -468,17 +486,21 @@ tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* leve
 }  // namespace
 
 tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st) {
+  TC_CUDA_TRY(cudaMemsetAsync(g->level, 0xFF, sizeof(int32_t) * g->n, st));
+  k_set_root<<<1, 1, 0, st>>>(g->level, g->queue_a, root); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  return run_bfs_from_queue(g, 1, st);
+}
+
+tc_status run_bfs_from_queue(tc_graph* g, uint64_t k, cudaStream_t st) {
   const uint32_t n = g->n;
   const int sms = num_sms();
   g->stats.bfs_steps = 0;
   g->stats.bottom_up_steps = 0;
   g->stats.restarted = 0;
   TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
-  TC_CUDA_TRY(cudaMemsetAsync(g->level, 0xFF, sizeof(int32_t) * n, st));
-  k_set_root<<<1, 1, 0, st>>>(g->level, g->queue_a, root); TC_LAUNCHED();
-  TC_CUDA_TRY(cudaGetLastError());
   uint32_t levels = 0;
-  TC_TRY(level_loop(g, 1, st, &levels));
+  TC_TRY(level_loop(g, k, st, &levels));
   g->stats.num_levels = levels;
 
   // restart phase

@@ -107,9 +107,16 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                                                        uint2* __restrict__ cover,
                                                        uint2* __restrict__ large,
                                                        uint32_t* __restrict__ ocount,
+                                                       const unsigned long long* __restrict__ voff,
+                                                       uint32_t nb,
+                                                       unsigned long long* __restrict__ gcount,
                                                        DevCounters* ctr) {
-  __shared__ uint32_t s_lo, s_hi;
+  __shared__ uint32_t s_lo, s_hi, s_g0, s_g1;
   Tally tl;
+  // batch mode: counts of the inline merges go to their graph, one atomic per
+  // run of edges of the same graph seen by this thread
+  uint32_t run_g = 0xFFFFFFFFu;
+  unsigned long long run = 0;
   for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
        e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
     const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
@@ -117,6 +124,10 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
     if (threadIdx.x == 0) {
       s_lo = row_of(row_ptr, 0, n - 1, e0);
       s_hi = row_of(row_ptr, s_lo, n - 1, e1 - 1);
+      if (nb) {
+        s_g0 = batch_graph_of(voff, 0, nb - 1, s_lo);
+        s_g1 = batch_graph_of(voff, s_g0, nb - 1, s_hi);
+      }
     }
     __syncthreads();
     const uint32_t lo = s_lo, hi = s_hi;
@@ -138,11 +149,17 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
             if (du <= small_max && dv <= small_max) {
               // two-pointer merge of N(u) and N(v)
               unsigned long long x = bu, y = bv;
+              uint32_t here = 0;
               while (x < eu && y < ev) {
                 const uint32_t a = col[x], c = col[y];
                 if (a == c) {
-                  if (level[a] != lu) ++tl.c1;
-                  else if (v < a) ++tl.c2c;
+                  if (level[a] != lu) {
+                    ++tl.c1;
+                    ++here;
+                  } else if (v < a) {
+                    ++tl.c2c;
+                    ++here;
+                  }
                   ++x;
                   ++y;
                 } else if (a < c) {
@@ -150,6 +167,15 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                 } else {
                   ++y;
                 }
+              }
+              if (nb && here) {
+                const uint32_t gid = s_g0 == s_g1 ? s_g0 : batch_graph_of(voff, s_g0, s_g1, u);
+                if (gid != run_g) {
+                  if (run) atomicAdd(&gcount[run_g], run);
+                  run_g = gid;
+                  run = 0;
+                }
+                run += here;
               }
             } else {
               is_large = true;
@@ -164,6 +190,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
       warp_append_pair(is_large, le, large, &ctr->num_large);
     }
   }
+  if (run) atomicAdd(&gcount[run_g], run);
   flush_tally(tl, ctr);
 }
 
@@ -405,15 +432,36 @@ __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_
 
 // The warp streams arr[cur, end) up to the first id above hi (kBounded; the
 // last chunk of a row is unbounded), looking every element up in the chunk;
-// returns the new cursor and adds the hits.  The next block of
-// kStreamUnroll x 32 elements is loaded before the current one is looked up.
-// Unbounded full blocks skip the end test.
+// returns the new cursor and adds the hits.
+//  - unbounded: blocks of kStreamUnroll x 32 elements, the next block loaded
+//    before the current one is looked up;
+//  - bounded: blocks of 32, the next one loaded early only while the current
+//    block ends at or below hi, so a pass reads at most 63 ids past its part
+//    (they are read again by the next chunk's pass).
 template <bool kBounded, bool kSorted>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, unsigned long long cur, const unsigned long long end,
     const uint32_t hi, const Cuckoo& ck, const uint32_t sorted_len, uint32_t& hits) {
   if (cur >= end) return end;
   const unsigned lane = lane_id();
+  if (kBounded) {
+    uint32_t w = lane < end - cur ? __ldg(arr + cur + lane) : kEmpty;
+    for (;;) {
+      const unsigned long long left = end - cur;
+      const uint32_t rem = left > 32ull ? 32u : (uint32_t)left;
+      const bool in = lane < rem && w <= hi;
+      const unsigned stop = __ballot_sync(0xffffffffu, !in);
+      const unsigned long long next = cur + 32ull;
+      uint32_t wn = kEmpty;
+      if (!stop && next < end) wn = lane < end - next ? __ldg(arr + next + lane) : kEmpty;
+      const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
+      if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w);
+      if (stop) return cur + take;
+      if (next >= end) return end;
+      cur = next;
+      w = wn;
+    }
+  }
   uint32_t w[kStreamUnroll];
   load_block(arr, cur, end, w);
   for (;;) {
@@ -421,7 +469,7 @@ __device__ __forceinline__ unsigned long long stream_segment(
     const bool more = next < end;
     uint32_t wn[kStreamUnroll];
     if (more) load_block(arr, next, end, wn);
-    if (!kBounded && more) {
+    if (more) {
 #pragma unroll
       for (int u = 0; u < kStreamUnroll; ++u) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
     } else {
@@ -430,14 +478,10 @@ __device__ __forceinline__ unsigned long long stream_segment(
 #pragma unroll
       for (int u = 0; u < kStreamUnroll; ++u) {
         const uint32_t j = lane + 32u * u;
-        const bool in = j < rem && (!kBounded || w[u] <= hi);
-        const unsigned stop = __ballot_sync(0xffffffffu, !in);
-        const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
-        if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
-        if (stop) return cur + 32ull * u + take;
+        if (j < rem) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
       }
+      return end;
     }
-    if (!more) return end;
     cur = next;
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) w[u] = wn[u];
@@ -490,7 +534,8 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
     const unsigned long long* __restrict__ ioff, const uint32_t* __restrict__ item_owner,
     unsigned long long nitems, uint32_t chunk, uint32_t per_item, uint32_t force_sorted,
-    DevCounters* ctr) {
+    const unsigned long long* __restrict__ voff, uint32_t nb,
+    unsigned long long* __restrict__ gcount, DevCounters* ctr) {
   extern __shared__ uint4 table4[];
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
@@ -509,6 +554,7 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     const unsigned long long hb = row_ptr[h], he = row_ptr[h + 1];
     const uint32_t chunks = (uint32_t)((he - hb + chunk - 1) / chunk);
     const unsigned long long eb = ooff[h] + (item - ioff[h]) * per_item;
+    unsigned long long item_hits = 0;  // this thread's hits in this item (batch mode)
     const uint32_t ne = (uint32_t)min((unsigned long long)per_item, ooff[h + 1] - eb);
     for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x) {
       const uint32_t x = ostream[eb + i];
@@ -567,8 +613,13 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
         }
         tl.c1 += c1;
         tl.c2c += c2c;
+        item_hits += c1 + c2c;
       }
       __syncthreads();
+    }
+    if (nb) {  // one atomic per warp per item into the owner's graph
+      item_hits = warp_sum(item_hits);
+      if (lane == 0 && item_hits) atomicAdd(&gcount[batch_graph_of(voff, 0, nb - 1, h)], item_hits);
     }
   }
   flush_tally(tl, ctr);
@@ -587,7 +638,8 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   const uint32_t small_max = g->params.small_max_degree;
   k_cover<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount, g->ctr); TC_LAUNCHED();
+      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount, g->voff,
+      g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
   TC_TRY(exclusive_scan_u32(g->ocount, g->ooff, n, g->scan, st));
@@ -651,7 +703,7 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   k_owner_hash<<<grid, kHashBlock, smem, st>>>(g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff,
                                               g->ostream, g->ioff, g->item_owner, nitems, chunk,
                                               per_item, g->params.sorted_lookup ? 1u : 0u,
-                                              g->ctr); TC_LAUNCHED();
+                                              g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

@@ -42,6 +42,8 @@ tc_status dalloc(T** p, size_t count) {
   return TC_OK;
 }
 
+}  // namespace
+
 void free_graph(tc_graph* g) {
   if (!g) return;
   void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
@@ -92,6 +94,8 @@ void params_default(tc_params* p) {
   p->persistent_bfs = 1;
   p->barrier_timeout_ms = 2000;
 }
+
+namespace {
 
 tc_status sync_status(tc_graph* g, cudaStream_t st) {
   cudaError_t e = cudaStreamSynchronize(st);
@@ -245,20 +249,6 @@ tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
   g->stats.hash_edges = c.num_large;
   g->counted = true;
   g->last_root = root;
-  return TC_OK;
-}
-
-tc_status tc_count_many(tc_graph* const* gs, const uint32_t* roots, size_t k, void* stream,
-                        uint64_t* counts) {
-  if (k == 0) return TC_OK;
-  if (!gs || !roots || !counts) return TC_ERR_INVALID_ARG;
-  for (size_t i = 0; i < k; ++i) {
-    if (!gs[i]) return TC_ERR_INVALID_ARG;
-    if (gs[i]->n > 0 && roots[i] >= gs[i]->n) return TC_ERR_INVALID_ARG;
-  }
-  std::vector<uint64_t> tmp(k);
-  for (size_t i = 0; i < k; ++i) TC_TRY(tc_count(gs[i], roots[i], stream, &tmp[i]));
-  for (size_t i = 0; i < k; ++i) counts[i] = tmp[i];
   return TC_OK;
 }
 

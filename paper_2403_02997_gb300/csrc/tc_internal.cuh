@@ -29,6 +29,8 @@ struct DevCounters {
   unsigned long long unvisited;  // vertices still unvisited
   unsigned long long plen[3];    // persistent BFS: frontier lengths, one slot per level mod 3
   unsigned long long pedges[3];  // persistent BFS: degree sums of those frontiers
+  unsigned int pmaxdeg[3];       // persistent BFS: largest degree in those frontiers
+  unsigned int fmaxdeg;          // largest degree of the current frontier (host-driven steps)
   unsigned int bar_count;        // grid barrier: blocks arrived
   unsigned int bar_gen;          // grid barrier: generation
   unsigned int p_level;          // persistent BFS: level of the frontier it stopped at
@@ -84,6 +86,12 @@ struct tc_graph {
   tc::ScanScratch scan;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
+  // batch mode: this handle is the disjoint union of batch_k graphs; vertex v
+  // belongs to graph g with voff[g] <= v < voff[g+1], whose count goes to gcount[g]
+  uint32_t batch_k = 0;
+  const unsigned long long* voff = nullptr;  // device, batch_k + 1
+  unsigned long long* gcount = nullptr;      // device, batch_k
+
   tc_params params;
   tc_stats stats;
   bool counted = false;
@@ -137,6 +145,22 @@ size_t scan_scratch_entries(uint64_t max_count);
 tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
                     cudaStream_t st);
 tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st);
+// BFS from the k roots already stored in queue_a (all at level 0, level[] set
+// to -1 elsewhere by the caller), then the restart rule.
+tc_status run_bfs_from_queue(tc_graph* g, uint64_t k, cudaStream_t st);
+tc_status alloc_count_state(tc_graph* g);
+void free_graph(tc_graph* g);
+void params_default(tc_params* p);
+
+// Graph of vertex (or entry) x in a batch: the largest g < nb with off[g] <= x.
+__device__ __forceinline__ uint32_t batch_graph_of(const unsigned long long* off, uint32_t lo,
+                                                   uint32_t hi, unsigned long long x) {
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (off[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
 
 // ---- device helpers -----------------------------------------------------
