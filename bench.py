@@ -50,6 +50,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="rmat24")
     p.add_argument("--batch-graphs", type=int, default=4096)
+    p.add_argument("--no-tuned", action="store_true",
+                   help="ignore the autotuner's table (paper_2403_02997_gb300/tuned_params.json)")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle intersection work in the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -370,7 +372,13 @@ def run_ours(args, world, rank, local):
     g = tc.Graph(d_src, d_dst, spec.n, stream=stream)
     del d_src, d_dst
     root = g.max_degree_vertex() if spec.root == "maxdeg" else 0
+    from paper_2403_02997_gb300 import autotune
+    tuned = None if args.no_tuned else autotune.lookup(
+        autotune.signature(spec.n, g.m, g.d_max, spec.family))
+    if tuned:
+        g.set_params(**tuned)
     params = tc.tc_params_default()
+    params.update(tuned or {})
 
     counts = []
     for _ in range(args.warmup):
@@ -456,7 +464,8 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generator)",
-        "config": config_dict(spec, args),
+        "config": dict(config_dict(spec, args), params=params,
+                       params_source="autotuned" if tuned else "defaults"),
         "triangles": T, "m": m, "num_cover": n_cover, "covering_ratio": n_cover / max(m, 1),
         "cover_intersections_per_s": n_cover / (statistics.mean(ms_inter) / 1e3)
         if statistics.mean(ms_inter) > 0 else None,
@@ -504,6 +513,11 @@ def run_batched(args, world, rank, local):
     roots = [g.max_degree_vertex() if sp.root == "maxdeg" else 0 for g, sp in zip(gs, specs)]
     m_total = sum(g.m for g in gs)
     b = tc.Batch(gs, stream=stream)
+    from paper_2403_02997_gb300 import autotune
+    tuned = None if args.no_tuned else autotune.lookup(autotune.signature(
+        sum(sp.n for sp in specs), m_total, max(g.d_max for g in gs), "batched", len(gs)))
+    if tuned:
+        b.set_params(**tuned)
     counts = None
     for _ in range(args.warmup):
         counts = b.count(roots, stream=stream)
@@ -557,7 +571,7 @@ def run_batched(args, world, rank, local):
                    "families": "even: ER mean degree U[4,64]; odd: R-MAT ef U{8..16}",
                    "master_seed": 4, "vertices": int(sum(sp.n for sp in specs)),
                    "edges_undirected": int(m_total), "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2"},
+                   "l2": "inputs larger than L2", "params": tuned or "defaults"},
         "edges_per_s": sum_over_ranks(float(m_total) * args.steps, world) / (ms / 1e3),
         "one_count_per_graph": {"graphs_per_s": len(gs) / t_single, "seconds": t_single},
         "speedup_vs_one_count_per_graph": (len(gs) / (ms / 1e3 / args.steps)) / (len(gs) / t_single),

@@ -1,0 +1,153 @@
+"""Autotuner for the count's tunables (tc_params).
+
+The tunables change speed only, never the count:
+- ``small_max_degree``: degree bound of the inline-merge bin;
+- ``hash_chunk``: owner-row entries per shared-memory table;
+- ``edges_per_item``: cover edges per owner-hash work item;
+- ``bfs_alpha`` / ``bfs_beta``: the direction switches of the BFS.
+
+``tune`` runs a coordinate descent. It starts from the defaults and, one parameter at a time, tries
+each candidate value. A value is kept only if the measured total time drops by more than
+``min_gain``. Every candidate's count must equal the default's. Times are the library's own
+CUDA-event totals (``ms_total`` of tc_stats), and the best of ``trials`` runs is kept.
+
+Results are cached in a JSON table keyed by a workload signature: family, log2 n, log2 m,
+log2 d_max, and batch size. ``lookup`` returns the tuned parameters for a signature, or None.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from typing import Dict, Iterable, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tuned_params.json")
+
+GRID: Dict[str, Sequence[int]] = {
+    "hash_chunk": (2048, 4096, 8192, 16384),
+    "edges_per_item": (64, 128, 256, 512),
+    "small_max_degree": (0, 8, 16, 32, 64, 128),
+    "bfs_alpha": (4, 15, 40),
+    "bfs_beta": (8, 18, 48),
+}
+ORDER = ("hash_chunk", "edges_per_item", "small_max_degree", "bfs_alpha", "bfs_beta")
+
+
+def signature(n: int, m: int, d_max: int, family: str = "", batch: int = 1) -> str:
+    lg = lambda x: int(round(math.log2(max(int(x), 1))))
+    return f"{family or 'graph'}:n{lg(n)}:m{lg(m)}:d{lg(d_max)}:k{lg(batch)}"
+
+
+def _measure(target, roots, params: dict, trials: int):
+    target.set_params(**params)
+    best, count = float("inf"), None
+    for _ in range(trials):
+        c = target.count(roots)
+        st = target.stats()
+        best = min(best, float(st["ms_total"]))
+        if count is None:
+            count = c
+        elif c != count:
+            raise RuntimeError("count changed between runs of one parameter set")
+    return best, count
+
+
+def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials: int = 2,
+         min_gain: float = 0.02, time_budget_s: float = 120.0) -> dict:
+    """Coordinate descent over `grid` for a tc.Graph (roots: int) or tc.Batch (roots: list)."""
+    from paper_2403_02997_gb300 import tc_params_default
+    grid = dict(GRID if grid is None else grid)
+    base = {k: v for k, v in tc_params_default().items()
+            if k in ("small_max_degree", "hash_chunk", "edges_per_item", "bfs_alpha", "bfs_beta")}
+    t0 = time.time()
+    best_ms, want = _measure(target, roots, base, trials)
+    history = [{"params": dict(base), "ms": best_ms}]
+    cur = dict(base)
+    for name in ORDER:
+        if name not in grid:
+            continue
+        for val in grid[name]:
+            if val == cur[name] or time.time() - t0 > time_budget_s:
+                continue
+            cand = dict(cur)
+            cand[name] = int(val)
+            try:
+                ms, got = _measure(target, roots, cand, trials)
+            except Exception as e:  # a value the library rejects is skipped
+                history.append({"params": cand, "error": str(e)})
+                continue
+            if got != want:
+                raise RuntimeError(f"count differs under {cand}: {got} != {want}")
+            history.append({"params": cand, "ms": ms})
+            if ms < best_ms * (1.0 - min_gain):
+                best_ms, cur = ms, cand
+    target.set_params(**cur)
+    return {"params": cur, "ms": best_ms, "default_ms": history[0]["ms"], "history": history,
+            "seconds": time.time() - t0}
+
+
+def load_cache(path: str = CACHE) -> dict:
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def store(sig: str, result: dict, path: str = CACHE) -> None:
+    table = load_cache(path)
+    table[sig] = {"params": result["params"], "ms": result["ms"],
+                  "default_ms": result["default_ms"]}
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
+def lookup(sig: str, path: str = CACHE) -> Optional[dict]:
+    entry = load_cache(path).get(sig)
+    return None if entry is None else dict(entry["params"])
+
+
+if __name__ == "__main__":
+    # Tune the named single-graph workloads and the batched one on this GPU.
+    import argparse
+
+    import numpy as np
+    import torch
+
+    import paper_2403_02997_gb300 as tc
+    from paper_2403_02997_gb300 import build, gen
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workloads", nargs="*", default=["rmat24", "batched"])
+    ap.add_argument("--trials", type=int, default=2)
+    ap.add_argument("--budget", type=float, default=150.0)
+    ap.add_argument("--out", default=CACHE, help="table to update (default: the package's)")
+    args = ap.parse_args()
+    build.build_all()
+    specs = {"rmat24": gen.RMAT_24, "rmat22": gen.rmat_spec(22, 16, 2), "mesh4096": gen.MESH_4096,
+             "er1024": gen.ER_1024}
+    for w in args.workloads:
+        if w == "batched":
+            sp = gen.batched_specs()
+            gs = [tc.Graph(*s.edges(), s.n) for s in sp]
+            roots = [g.max_degree_vertex() if s.root == "maxdeg" else 0 for g, s in zip(gs, sp)]
+            target = tc.Batch(gs)
+            sig = signature(sum(s.n for s in sp), sum(g.m for g in gs), max(g.d_max for g in gs),
+                            "batched", len(gs))
+            for g in gs:
+                g.close()
+        else:
+            s = specs[w]
+            src, dst = s.edges()
+            target = tc.Graph(torch.from_numpy(src.view(np.int32)).cuda(),
+                              torch.from_numpy(dst.view(np.int32)).cuda(), s.n)
+            roots = target.max_degree_vertex() if s.root == "maxdeg" else 0
+            sig = signature(s.n, target.m, target.d_max, s.family)
+        res = tune(target, roots, trials=args.trials, time_budget_s=args.budget)
+        store(sig, res, args.out)
+        print(json.dumps({"workload": w, "signature": sig, "params": res["params"],
+                          "ms": res["ms"], "default_ms": res["default_ms"],
+                          "seconds": round(res["seconds"], 1)}), flush=True)
+        target.close()

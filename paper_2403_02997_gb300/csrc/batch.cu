@@ -21,7 +21,7 @@
 struct tc_batch {
   tc_graph* u = nullptr;                   // the union (owns its CSR and count state)
   uint32_t k = 0;
-  std::vector<tc_graph*> parts;
+  std::vector<uint32_t> part_n;            // vertices of each graph (the handles are not kept)
   std::vector<unsigned long long> voff_h;  // k + 1
   unsigned long long* voff = nullptr;      // device copies
   unsigned long long* eoff = nullptr;
@@ -121,7 +121,8 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
   tc_batch* b = new (std::nothrow) tc_batch();
   if (!b) return TC_ERR_OOM;
   b->k = (uint32_t)k;
-  b->parts.assign(gs, gs + k);
+  b->part_n.resize(k);
+  for (size_t i = 0; i < k; ++i) b->part_n[i] = gs[i]->n;
   std::vector<unsigned long long> voff(k + 1, 0), eoff(k + 1, 0);
   uint32_t dmax = 0;
   for (size_t i = 0; i < k; ++i) {
@@ -218,7 +219,7 @@ tc_status tc_batch_count(tc_batch* b, const uint32_t* roots, void* stream, uint6
   std::vector<uint32_t> ur;
   ur.reserve(k);
   for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t n = b->parts[i]->n;
+    const uint32_t n = b->part_n[i];
     if (n == 0) continue;
     if (roots[i] >= n) return TC_ERR_INVALID_ARG;
     ur.push_back((uint32_t)(b->voff_h[i] + roots[i]));
@@ -276,9 +277,10 @@ tc_status tc_batch_get_stats(const tc_batch* b, tc_stats* out) {
 }
 
 tc_status tc_batch_get_levels(const tc_batch* b, size_t i, int32_t* host_levels) {
-  if (!b || !host_levels || i >= b->k || !b->u->counted) return TC_ERR_INVALID_ARG;
-  const uint32_t n = b->parts[i]->n;
+  if (!b || i >= b->k || !b->u->counted) return TC_ERR_INVALID_ARG;
+  const uint32_t n = b->part_n[i];
   if (n == 0) return TC_OK;
+  if (!host_levels) return TC_ERR_INVALID_ARG;
   TC_CUDA_TRY(cudaDeviceSynchronize());
   std::vector<int32_t> tmp(n);
   TC_CUDA_TRY(cudaMemcpy(tmp.data(), b->u->level + b->voff_h[i], sizeof(int32_t) * n,

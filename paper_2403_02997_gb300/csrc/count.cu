@@ -432,41 +432,22 @@ __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_
 
 // The warp streams arr[cur, end) up to the first id above hi (kBounded; the
 // last chunk of a row is unbounded), looking every element up in the chunk;
-// returns the new cursor and adds the hits.
-//  - unbounded: blocks of kStreamUnroll x 32 elements, the next block loaded
-//    before the current one is looked up;
-//  - bounded: blocks of 32, the next one loaded early only while the current
-//    block ends at or below hi, so a pass reads at most 63 ids past its part
-//    (they are read again by the next chunk's pass).
+// returns the new cursor and adds the hits.  Blocks of kStreamUnroll x 32
+// elements; the next block is loaded before the current one is looked up --
+// in a bounded pass only while the current block ends at or below hi, so a
+// pass reads at most one block past its part (re-read by the next chunk).
 template <bool kBounded, bool kSorted>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, unsigned long long cur, const unsigned long long end,
     const uint32_t hi, const Cuckoo& ck, const uint32_t sorted_len, uint32_t& hits) {
   if (cur >= end) return end;
   const unsigned lane = lane_id();
-  if (kBounded) {
-    uint32_t w = lane < end - cur ? __ldg(arr + cur + lane) : kEmpty;
-    for (;;) {
-      const unsigned long long left = end - cur;
-      const uint32_t rem = left > 32ull ? 32u : (uint32_t)left;
-      const bool in = lane < rem && w <= hi;
-      const unsigned stop = __ballot_sync(0xffffffffu, !in);
-      const unsigned long long next = cur + 32ull;
-      uint32_t wn = kEmpty;
-      if (!stop && next < end) wn = lane < end - next ? __ldg(arr + next + lane) : kEmpty;
-      const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
-      if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w);
-      if (stop) return cur + take;
-      if (next >= end) return end;
-      cur = next;
-      w = wn;
-    }
-  }
   uint32_t w[kStreamUnroll];
   load_block(arr, cur, end, w);
   for (;;) {
     const unsigned long long next = cur + 32ull * kStreamUnroll;
-    const bool more = next < end;
+    bool more = next < end;
+    if (kBounded) more = more && __shfl_sync(0xffffffffu, w[kStreamUnroll - 1], 31) <= hi;
     uint32_t wn[kStreamUnroll];
     if (more) load_block(arr, next, end, wn);
     if (more) {
@@ -478,8 +459,13 @@ __device__ __forceinline__ unsigned long long stream_segment(
 #pragma unroll
       for (int u = 0; u < kStreamUnroll; ++u) {
         const uint32_t j = lane + 32u * u;
-        if (j < rem) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
+        const bool in = j < rem && (!kBounded || w[u] <= hi);
+        const unsigned stop = __ballot_sync(0xffffffffu, !in);
+        const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
+        if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
+        if (stop) return cur + 32ull * u + take;
       }
+      // the whole block was in range; it was the last one of the segment
       return end;
     }
     cur = next;
