@@ -28,7 +28,7 @@ CACHE = os.path.join(HERE, "tuned_params.json")
 GRID: Dict[str, Sequence[int]] = {
     "hash_chunk": (2048, 4096, 8192, 16384),
     "edges_per_item": (64, 128, 256, 512),
-    "small_max_degree": (0, 8, 16, 32, 64, 128),
+    "small_max_degree": (0, 8, 16, 32, 64, 128, 256, 512, 1024),
     "bfs_alpha": (4, 15, 40),
     "bfs_beta": (8, 18, 48),
 }
