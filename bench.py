@@ -48,7 +48,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="rmat24")
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve"], default="rmat24")
+    p.add_argument("--serve-requests", type=int, default=2000,
+                   help="requests per arrival-rate point of the serving sweep")
+    p.add_argument("--serve-budget-gb", type=float, default=96.0)
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--no-tuned", action="store_true",
                    help="ignore the autotuner's table (paper_2403_02997_gb300/tuned_params.json)")
@@ -589,18 +592,73 @@ def run_batched(args, world, rank, local):
     return 0
 
 
+def run_serve(args, world, rank, local):
+    """The serving workload: Poisson arrivals of count requests.
+
+    Requests are drawn from the batched distribution, a pool of 512 graphs with n log-uniform on
+    [2^6, 2^16], seed 5. Every 100th request is an R-MAT scale-22, edge-factor-16 graph, which is
+    the 1 %. The capacity is first measured with every request arriving at once. The sweep then
+    runs at 0.1, 0.3, 0.6, 0.9 and 1.2 times that capacity and reports graphs/s and p50/p99
+    latency from arrival to count.
+    """
+    import torch
+    from paper_2403_02997_gb300 import autotune, build as tcbuild, serve
+    tcbuild.build_all()
+    torch.cuda.set_device(local)
+    specs = gen.batched_specs(512, master_seed=5 + 1000 * rank)
+    pool = [(*sp.edges(), sp.n, None if sp.root == "maxdeg" else 0) for sp in specs]
+    big = [(*gen.rmat_spec(22, 16, 22 + i + 1000 * rank).edges(), 1 << 22, None) for i in range(2)]
+    tuned = None if args.no_tuned else autotune.lookup("batched:n25:m29:d13:k12")
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = serve.Server(hbm_budget_bytes=budget, params=tuned)
+    serve.run_arrivals(srv, pool, rate=1e6, count=200, seed=1)          # warm-up
+    sat = serve.run_arrivals(srv, pool, rate=1e9, count=args.serve_requests, seed=2,
+                             big_every=100, big_pool=big)
+    capacity = sat["graphs_per_s"]
+    points = []
+    for f in (0.1, 0.3, 0.6, 0.9, 1.2):
+        r = serve.run_arrivals(srv, pool, rate=f * capacity, count=args.serve_requests,
+                               seed=int(100 * f), big_every=100, big_pool=big)
+        r.pop("requests_list")
+        r["load"] = f
+        points.append(r)
+    batches = list(srv.batches)
+    srv.close()
+    if rank != 0:
+        return 0
+    knee = next((p["load"] for p in points if p["p99_ms"] and points[0]["p99_ms"] and
+                 p["p99_ms"] > 5 * points[0]["p99_ms"]), None)
+    line = {
+        "metric": "served graphs/s and p50/p99 latency (continuous batching, Poisson arrivals)",
+        "value": max(p["graphs_per_s"] for p in points), "unit": "graphs/s", "n_gpus": world,
+        "steps": len(points), "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": "serve", "pool": "512 graphs, n log-uniform [2^6, 2^16] (seed 5)",
+                   "big": "1 % R-MAT scale 22 ef 16", "requests_per_point": args.serve_requests,
+                   "hbm_budget_gb": args.serve_budget_gb, "params": tuned or "defaults"},
+        "capacity_graphs_per_s": capacity, "saturated_p50_ms": sat["p50_ms"],
+        "saturated_p99_ms": sat["p99_ms"], "sweep": points, "p99_knee_load": knee,
+        "mean_batch": float(np.mean(batches)) if batches else None,
+        "max_batch": int(max(batches)) if batches else None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
-            if args.workload == "batched":
+            if args.workload in ("batched", "serve"):
                 print(json.dumps({"impl": "reference", "unavailable":
-                                  "the batched workload is timed for the GPU arm only"}))
+                                  f"the {args.workload} workload is timed for the GPU arm only"}))
                 return 0
             return run_reference(args, world, rank)
         if args.workload == "batched":
             return run_batched(args, world, rank, local)
+        if args.workload == "serve":
+            return run_serve(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -1,0 +1,210 @@
+"""Continuous-batching triangle-count service on one GPU.
+
+A request is one graph (an edge list on the host, its vertex count and a root
+rule).
+
+- The **admission** thread takes requests in arrival order. A request is admitted while its HBM
+  footprint fits the budget next to everything already resident. The thread then builds its graph
+  on the device on its own stream (host-to-device copy and CSR build) and queues it as ready.
+- The **counting** thread takes every ready graph (up to ``max_batch``) and counts them together as
+  one batch: one concatenated CSR, one multi-source BFS, one pass of each count kernel. It then
+  answers each request and frees the graphs. The memory returns to the budget for the next
+  admissions.
+
+While a batch is on the device, newly arrived graphs are being admitted and built for the next one.
+Building and counting overlap; a request never waits for a fixed batch size.
+
+Latency is measured from arrival to the moment the count is on the host; p50 / p99 come from the
+completed requests.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+import paper_2403_02997_gb300 as tc
+
+
+def footprint_bytes(n: int, draws: int) -> int:
+    """Device bytes one request may hold.
+
+    This counts the graph handle (CSR + per-count state, with m <= draws undirected edges), its
+    share of the batch union (a second copy of the same), and the transient sort buffers of the
+    build (two arrays of 2·draws 8-byte keys plus the staged edge list).
+    """
+    per_graph = 8 * (n + 1) + 4 * (2 * draws + 8) + 68 * n + 36 * draws
+    transient = 32 * draws + 8 * draws
+    return 2 * per_graph + transient + (1 << 16)
+
+
+@dataclass
+class Request:
+    rid: int
+    src: np.ndarray
+    dst: np.ndarray
+    n: int
+    root: Optional[int] = None          # None: the smallest id of largest degree
+    arrival: float = 0.0                # time.perf_counter() at arrival
+    done: float = 0.0
+    count: Optional[int] = None
+    error: Optional[str] = None
+    bytes: int = 0
+    event: threading.Event = field(default_factory=threading.Event)
+
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, max_batch: int = 4096, params=None):
+        import torch
+        self.budget = int(hbm_budget_bytes)
+        self.max_batch = max_batch
+        self.params = dict(params or {})
+        self.build_stream = torch.cuda.Stream()
+        self.count_stream = torch.cuda.Stream()
+        self.lock = threading.Condition()
+        self.pending: deque = deque()     # arrived, not admitted
+        self.ready: List = []             # (request, graph, root) built, waiting for a batch
+        self.used = 0
+        self.peak_used = 0
+        self.completed: List[Request] = []
+        self.batches: List[int] = []
+        self.stopping = False
+        self.threads = [threading.Thread(target=self._admit_loop, daemon=True),
+                        threading.Thread(target=self._count_loop, daemon=True)]
+        for t in self.threads:
+            t.start()
+
+    # -- client side ----------------------------------------------------------
+    def submit(self, req: Request) -> Request:
+        req.bytes = footprint_bytes(req.n, int(req.src.size))
+        if req.bytes > self.budget:
+            req.error = "request larger than the HBM budget"
+            req.done = time.perf_counter()
+            req.event.set()
+            return req
+        with self.lock:
+            self.pending.append(req)
+            self.lock.notify_all()
+        return req
+
+    def close(self) -> None:
+        with self.lock:
+            self.stopping = True
+            self.lock.notify_all()
+        for t in self.threads:
+            t.join()
+
+    # -- admission ------------------------------------------------------------
+    def _admit_loop(self) -> None:
+        while True:
+            with self.lock:
+                while not self.stopping and (not self.pending or
+                                             self.used + self.pending[0].bytes > self.budget):
+                    self.lock.wait(0.05)
+                if self.stopping and not self.pending:
+                    return
+                if self.used + self.pending[0].bytes > self.budget:
+                    continue
+                req = self.pending.popleft()
+                self.used += req.bytes
+                self.peak_used = max(self.peak_used, self.used)
+            try:
+                g = tc.Graph(req.src, req.dst, req.n, stream=self.build_stream)
+                if self.params:
+                    g.set_params(**self.params)
+                root = g.max_degree_vertex() if req.root is None else req.root
+                with self.lock:
+                    self.ready.append((req, g, root))
+                    self.lock.notify_all()
+            except Exception as e:  # the request fails alone; its memory returns
+                req.error = str(e)
+                req.done = time.perf_counter()
+                req.event.set()
+                with self.lock:
+                    self.used -= req.bytes
+                    self.lock.notify_all()
+
+    # -- counting -------------------------------------------------------------
+    def _count_loop(self) -> None:
+        while True:
+            with self.lock:
+                while not self.ready and not (self.stopping and not self.pending):
+                    self.lock.wait(0.05)
+                if not self.ready and self.stopping and not self.pending:
+                    return
+                take = self.ready[: self.max_batch]
+                del self.ready[: len(take)]
+            reqs = [t[0] for t in take]
+            graphs = [t[1] for t in take]
+            roots = [t[2] for t in take]
+            try:
+                if len(graphs) == 1:
+                    counts = [graphs[0].count(roots[0], stream=self.count_stream)]
+                else:
+                    b = tc.Batch(graphs, stream=self.count_stream)
+                    if self.params:
+                        b.set_params(**self.params)
+                    counts = b.count(roots, stream=self.count_stream)
+                    b.close()
+                err = None
+            except Exception as e:
+                counts, err = [None] * len(graphs), str(e)
+            now = time.perf_counter()
+            for r, g, c in zip(reqs, graphs, counts):
+                g.close()
+                r.count, r.error, r.done = c, err, now
+                r.event.set()
+            with self.lock:
+                self.used -= sum(r.bytes for r in reqs)
+                self.completed.extend(reqs)
+                self.batches.append(len(reqs))
+                self.lock.notify_all()
+
+
+def percentile(xs, q):
+    if not xs:
+        return None
+    return float(np.percentile(np.asarray(xs), q))
+
+
+def run_arrivals(server: Server, pool: list, rate: float, count: int, seed: int = 5,
+                 big_every: int = 0, big_pool: Optional[list] = None) -> dict:
+    """Poisson arrivals at `rate` graphs/s of `count` requests drawn from `pool`.
+
+    A pool entry is ``(src, dst, n, root)``. With ``big_every`` = k, every k-th request is drawn from
+    ``big_pool`` instead (the 1 % of large graphs). The call blocks until all requests have been
+    answered.
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    picks = rng.integers(0, len(pool), size=count)
+    reqs = []
+    t0 = time.perf_counter()
+    next_t = t0
+    for i in range(count):
+        next_t += gaps[i]
+        while True:
+            now = time.perf_counter()
+            if now >= next_t:
+                break
+            time.sleep(min(next_t - now, 0.002))
+        use_big = big_every and big_pool and (i % big_every == big_every - 1)
+        src, dst, n, root = (big_pool[i % len(big_pool)] if use_big else pool[picks[i]])
+        r = Request(rid=i, src=src, dst=dst, n=n, root=root, arrival=time.perf_counter())
+        reqs.append(server.submit(r))
+    for r in reqs:
+        r.event.wait()
+    t1 = max(r.done for r in reqs)
+    lat = [1e3 * r.latency() for r in reqs if r.error is None]
+    return {"rate": rate, "requests": count, "errors": sum(r.error is not None for r in reqs),
+            "seconds": t1 - t0, "graphs_per_s": count / (t1 - t0),
+            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "mean_ms": float(np.mean(lat)) if lat else None, "requests_list": reqs}
