@@ -550,15 +550,25 @@ def run_batched(args, world, rank, local):
     t_single = time.perf_counter() - t0
     assert single == counts
     b.close()
-    # end to end: host edge lists -> graphs -> one batched count -> host counts
+    # end to end: host edge lists -> one batch built from them -> count -> host counts
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eb = tc.Batch.from_edges([(s, d, sp.n) for sp, (s, d) in zip(specs, edges)], stream=stream)
+    if tuned:
+        eb.set_params(**tuned)
+    e2e_counts = eb.count(roots, stream=stream)
+    eb.close()
+    t_e2e = time.perf_counter() - t0
+    assert e2e_counts == counts
+    # the same through per-graph handles and tc_count_many
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hs = [tc.Graph(s, d, sp.n, stream=stream) for sp, (s, d) in zip(specs, edges)]
-    e2e_counts = tc.count_many(hs, roots, stream=stream)
+    many_counts = tc.count_many(hs, roots, stream=stream)
     for h in hs:
         h.close()
-    t_e2e = time.perf_counter() - t0
-    assert e2e_counts == counts
+    t_many = time.perf_counter() - t0
+    assert many_counts == counts
     for g in gs:
         g.close()
     if rank != 0:
@@ -584,7 +594,9 @@ def run_batched(args, world, rank, local):
         "graph_build_seconds": t_create,
         "e2e": {"value": len(gs) / t_e2e, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 8 * len(gs), "seconds_per_step": t_e2e,
-                "what": "tc_graph_create from host edge lists for every graph + tc_count_many"},
+                "what": "host edge lists -> tc_batch_create_from_edges -> tc_batch_count"},
+        "e2e_per_graph_handles": {"graphs_per_s": len(gs) / t_many, "seconds": t_many,
+                                  "what": "tc_graph_create per graph + tc_count_many"},
         "gpu_launches": st["launches"] * args.steps,
         "clocks": clk,
     }

@@ -186,6 +186,22 @@ tc_status tc_set_params(tc_graph* g, const tc_params* p);
  */
 typedef struct tc_batch tc_batch;
 tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch** out);
+/*
+ * A batch straight from k graphs' edge lists, without per-graph handles: the
+ * edges of graph i are src[j], dst[j] for edge_offsets[i] <= j < edge_offsets[i+1]
+ * (edge_offsets: host, k+1 entries, edge_offsets[0] == 0), with local ids below
+ * num_vertices[i] (host, k entries).  src/dst are device arrays if
+ * edges_on_device != 0, else host arrays; they are copied.  One radix sort
+ * canonicalises every graph at once (self-loops dropped, repeats collapsed,
+ * rows sorted), exactly as tc_graph_create does per graph.  Errors as
+ * tc_batch_create, plus TC_ERR_VERTEX_RANGE when an id is >= its own graph's
+ * vertex count.
+ */
+tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
+                                     const uint64_t* edge_offsets, const uint32_t* num_vertices,
+                                     size_t k, int edges_on_device, void* stream, tc_batch** out);
+/* host_roots[i] = smallest local id of largest degree in graph i (0 if empty). */
+tc_status tc_batch_max_degree_vertices(tc_batch* b, void* stream, uint32_t* host_roots);
 /* roots[i] < n_i of graph i (ignored for empty graphs); counts: host, k entries. */
 tc_status tc_batch_count(tc_batch* b, const uint32_t* roots, void* stream, uint64_t* counts);
 tc_status tc_batch_set_params(tc_batch* b, const tc_params* p);

@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH):
         "tc_batch_get_stats": ([vp, P(tc_stats)], ctypes.c_int),
         "tc_batch_get_levels": ([vp, ctypes.c_size_t, vp], ctypes.c_int),
         "tc_batch_destroy": ([vp], ctypes.c_int),
+        "tc_batch_create_from_edges": ([vp, vp, P(u64), P(u32), ctypes.c_size_t, ctypes.c_int,
+                                        vp, P(vp)], ctypes.c_int),
+        "tc_batch_max_degree_vertices": ([vp, vp, P(u32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -308,6 +311,36 @@ class Batch:
         _check(lib.tc_batch_create(hs, self.k, _stream_handle(stream), ctypes.byref(out)),
                "tc_batch_create")
         self.handle = out.value
+
+    @classmethod
+    def from_edges(cls, graphs, stream=None) -> "Batch":
+        """Build a batch straight from host edge lists: graphs = [(src, dst, n), ...]."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self.k = len(graphs)
+        self.sizes = [int(n) for _, _, n in graphs]
+        lens = [int(np.asarray(s_).size) for s_, _, _ in graphs]
+        offs = np.zeros(self.k + 1, dtype=np.uint64)
+        offs[1:] = np.cumsum(lens, dtype=np.uint64)
+        src = np.concatenate([np.asarray(s_, np.uint32) for s_, _, _ in graphs]) if lens else \
+            np.zeros(0, np.uint32)
+        dst = np.concatenate([np.asarray(d_, np.uint32) for _, d_, _ in graphs]) if lens else \
+            np.zeros(0, np.uint32)
+        nv = np.asarray(self.sizes, dtype=np.uint32)
+        out = ctypes.c_void_p()
+        _check(lib.tc_batch_create_from_edges(
+            src.ctypes.data if src.size else None, dst.ctypes.data if dst.size else None,
+            offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+            nv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), self.k, 0,
+            _stream_handle(stream), ctypes.byref(out)), "tc_batch_create_from_edges")
+        self.handle = out.value
+        return self
+
+    def max_degree_vertices(self, stream=None) -> list:
+        out = (ctypes.c_uint32 * self.k)()
+        _check(load_library().tc_batch_max_degree_vertices(self.handle, _stream_handle(stream), out),
+               "tc_batch_max_degree_vertices")
+        return [int(x) for x in out]
 
     def count(self, roots: Sequence[int], stream=None) -> list:
         rs = (ctypes.c_uint32 * self.k)(*roots)

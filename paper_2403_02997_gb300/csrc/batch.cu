@@ -85,6 +85,46 @@ __global__ void k_seed_roots(const uint32_t* __restrict__ roots, uint32_t k, int
   }
 }
 
+// Largest (degree, -local id) per graph: after the pass, best[g] >> 32 is the
+// largest degree of graph g and ~best[g] & 0xFFFFFFFF its smallest such id.
+__global__ void __launch_bounds__(kGatherBlock) k_batch_maxdeg(
+    const unsigned long long* __restrict__ row_ptr, const unsigned long long* __restrict__ voff,
+    uint32_t k, unsigned long long N, unsigned long long* best) {
+  __shared__ uint32_t s_g0, s_g1;
+  for (unsigned long long t0 = (unsigned long long)blockIdx.x * kGatherTile; t0 < N;
+       t0 += (unsigned long long)gridDim.x * kGatherTile) {
+    const unsigned long long t1 = min(N, t0 + kGatherTile);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_g0 = batch_graph_of(voff, 0, k - 1, t0);
+      s_g1 = batch_graph_of(voff, s_g0, k - 1, t1 - 1);
+    }
+    __syncthreads();
+    const uint32_t g0 = s_g0, g1 = s_g1;
+    for (unsigned long long v = t0 + threadIdx.x; v < t1; v += kGatherBlock) {
+      const uint32_t g = g0 == g1 ? g0 : batch_graph_of(voff, g0, g1, v);
+      const unsigned long long deg = row_ptr[v + 1] - row_ptr[v];
+      const unsigned long long key = (deg << 32) | (0xFFFFFFFFull - (v - voff[g]));
+      atomicMax(&best[g], key);
+    }
+  }
+}
+
+// Counters, pinned mirror and events of a union handle.
+tc_status init_union(tc_graph* u) {
+  params_default(&u->params);
+  std::memset(&u->stats, 0, sizeof(u->stats));
+  if (cudaMalloc(&u->ctr, sizeof(DevCounters)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&u->ctr_host), sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_OOM;
+  }
+  std::memset(u->ctr_host, 0, sizeof(DevCounters));
+  for (cudaEvent_t& e : u->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return TC_ERR_CUDA;
+  return TC_OK;
+}
+
 void free_batch(tc_batch* b) {
   if (!b) return;
   if (b->u) {
@@ -141,16 +181,13 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
     tc_graph* u = new (std::nothrow) tc_graph();
     if (!u) { s = TC_ERR_OOM; break; }
     b->u = u;
-    params_default(&u->params);
-    std::memset(&u->stats, 0, sizeof(u->stats));
+    if ((s = init_union(u)) != TC_OK) break;
     u->n = (uint32_t)voff[k];
     u->nnz = eoff[k];
     u->m = u->nnz / 2;
     u->d_max = dmax;
     const size_t col_alloc = ((size_t)u->nnz + 7) & ~(size_t)3;
-    if (cudaMalloc(&u->ctr, sizeof(DevCounters)) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&u->ctr_host), sizeof(DevCounters)) != cudaSuccess ||
-        cudaMalloc(&u->row_ptr, sizeof(unsigned long long) * (voff[k] + 1)) != cudaSuccess ||
+    if (cudaMalloc(&u->row_ptr, sizeof(unsigned long long) * (voff[k] + 1)) != cudaSuccess ||
         cudaMalloc(&u->col, sizeof(uint32_t) * col_alloc) != cudaSuccess ||
         cudaMalloc(&b->voff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
         cudaMalloc(&b->eoff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
@@ -161,10 +198,6 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
       s = TC_ERR_OOM;
       break;
     }
-    std::memset(u->ctr_host, 0, sizeof(DevCounters));
-    bool ev_ok = true;
-    for (cudaEvent_t& e : u->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
-    if (!ev_ok) { s = TC_ERR_CUDA; break; }
     std::vector<PartDesc> pd(k);
     for (size_t i = 0; i < k; ++i) pd[i] = PartDesc{gs[i]->row_ptr, gs[i]->col};
     if (cudaMemcpyAsync(d_parts, pd.data(), sizeof(PartDesc) * k, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -196,6 +229,107 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
     return s;
   }
   *out = b;
+  return TC_OK;
+}
+
+tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
+                                     const uint64_t* edge_offsets, const uint32_t* num_vertices,
+                                     size_t k, int edges_on_device, void* stream, tc_batch** out) {
+  if (!out) return TC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (k == 0 || k > 0xFFFFFFFFull || !edge_offsets || !num_vertices || edge_offsets[0] != 0)
+    return TC_ERR_INVALID_ARG;
+  for (size_t i = 0; i < k; ++i)
+    if (edge_offsets[i + 1] < edge_offsets[i]) return TC_ERR_INVALID_ARG;
+  const uint64_t E = edge_offsets[k];
+  if (E > 0 && (!src || !dst)) return TC_ERR_INVALID_ARG;
+  if (E > (1ull << 34)) return TC_ERR_OVERFLOW;
+  std::vector<unsigned long long> voff(k + 1, 0);
+  for (size_t i = 0; i < k; ++i) voff[i + 1] = voff[i] + num_vertices[i];
+  if (voff[k] >= 0x80000000ull) return TC_ERR_OVERFLOW;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tc_batch* b = new (std::nothrow) tc_batch();
+  if (!b) return TC_ERR_OOM;
+  b->k = (uint32_t)k;
+  b->part_n.assign(num_vertices, num_vertices + k);
+  b->voff_h = voff;
+  tc_status s = TC_OK;
+  uint32_t *staged_src = nullptr, *staged_dst = nullptr, *d_nvert = nullptr;
+  do {
+    tc_graph* u = new (std::nothrow) tc_graph();
+    if (!u) { s = TC_ERR_OOM; break; }
+    b->u = u;
+    if ((s = init_union(u)) != TC_OK) break;
+    u->n = (uint32_t)voff[k];
+    if (cudaMalloc(&b->voff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
+        cudaMalloc(&b->eoff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
+        cudaMalloc(&b->gcount, sizeof(unsigned long long) * k) != cudaSuccess ||
+        cudaMalloc(&b->roots, sizeof(uint32_t) * k) != cudaSuccess ||
+        cudaMalloc(&d_nvert, sizeof(uint32_t) * k) != cudaSuccess) {
+      cudaGetLastError();
+      s = TC_ERR_OOM;
+      break;
+    }
+    // b->eoff holds the input edge offsets during the build
+    if (cudaMemcpyAsync(b->voff, voff.data(), sizeof(unsigned long long) * (k + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->eoff, edge_offsets, sizeof(unsigned long long) * (k + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_nvert, num_vertices, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      s = TC_ERR_CUDA;
+      break;
+    }
+    const uint32_t* d_src = src;
+    const uint32_t* d_dst = dst;
+    if (E > 0 && !edges_on_device) {
+      if (cudaMalloc(&staged_src, sizeof(uint32_t) * E) != cudaSuccess ||
+          cudaMalloc(&staged_dst, sizeof(uint32_t) * E) != cudaSuccess) {
+        cudaGetLastError();
+        s = TC_ERR_OOM;
+        break;
+      }
+      if (cudaMemcpyAsync(staged_src, src, sizeof(uint32_t) * E, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(staged_dst, dst, sizeof(uint32_t) * E, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        s = TC_ERR_CUDA;
+        break;
+      }
+      d_src = staged_src;
+      d_dst = staged_dst;
+    }
+    const EdgeGroups grp{b->eoff, b->voff, d_nvert, b->k};
+    if ((s = build_csr(u, d_src, d_dst, E, st, &grp)) != TC_OK) break;
+    if ((s = alloc_count_state(u)) != TC_OK) break;
+    u->batch_k = b->k;
+    u->voff = b->voff;
+    u->gcount = b->gcount;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { s = TC_ERR_CUDA; break; }
+  } while (0);
+  cudaStreamSynchronize(st);
+  cudaFree(staged_src);
+  cudaFree(staged_dst);
+  cudaFree(d_nvert);
+  if (s != TC_OK) {
+    free_batch(b);
+    return s;
+  }
+  *out = b;
+  return TC_OK;
+}
+
+tc_status tc_batch_max_degree_vertices(tc_batch* b, void* stream, uint32_t* host_roots) {
+  if (!b || !host_roots) return TC_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tc_graph* u = b->u;
+  std::vector<unsigned long long> best(b->k, 0);
+  if (u->n > 0) {
+    TC_CUDA_TRY(cudaMemsetAsync(b->gcount, 0, sizeof(unsigned long long) * b->k, st));
+    k_batch_maxdeg<<<grid_for(u->n, kGatherTile, num_sms() * 16), kGatherBlock, 0, st>>>(
+        u->row_ptr, b->voff, b->k, u->n, b->gcount);
+    TC_CUDA_TRY(cudaGetLastError());
+    TC_CUDA_TRY(cudaMemcpyAsync(best.data(), b->gcount, sizeof(unsigned long long) * b->k,
+                                cudaMemcpyDeviceToHost, st));
+    TC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (uint32_t i = 0; i < b->k; ++i)
+    host_roots[i] = b->part_n[i] ? (uint32_t)(0xFFFFFFFFull - (best[i] & 0xFFFFFFFFull)) : 0u;
   return TC_OK;
 }
 

@@ -40,6 +40,43 @@ __global__ void k_make_keys(const uint32_t* __restrict__ src, const uint32_t* __
   }
 }
 
+// The same for several graphs' edges in one array (EdgeGroups): a block takes a
+// tile of edges and finds the graphs at its two ends once; each endpoint is
+// checked against its own graph's vertex count and offset into the union.
+constexpr unsigned long long kKeyTile = 2048;
+__global__ void k_make_keys_multi(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                  uint64_t E, EdgeGroups grp, int kb,
+                                  ulonglong2* __restrict__ keys, DevCounters* ctr) {
+  __shared__ uint32_t s_g0, s_g1;
+  for (unsigned long long t0 = (unsigned long long)blockIdx.x * kKeyTile; t0 < E;
+       t0 += (unsigned long long)gridDim.x * kKeyTile) {
+    const unsigned long long t1 = min((unsigned long long)E, t0 + kKeyTile);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_g0 = batch_graph_of(grp.ein, 0, grp.k - 1, t0);
+      s_g1 = batch_graph_of(grp.ein, s_g0, grp.k - 1, t1 - 1);
+    }
+    __syncthreads();
+    const uint32_t g0 = s_g0, g1 = s_g1;
+    for (unsigned long long i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
+      const uint32_t g = g0 == g1 ? g0 : batch_graph_of(grp.ein, g0, g1, i);
+      const uint32_t u = src[i], v = dst[i], ng = grp.nvert[g];
+      const unsigned long long off = grp.voff[g];
+      ulonglong2 k;
+      if (u >= ng || v >= ng) {
+        atomicOr(&ctr->err, kErrVertexRange);
+        k.x = k.y = kSentinel;
+      } else if (u == v) {
+        k.x = k.y = kSentinel;
+      } else {
+        k.x = ((off + u) << kb) | (off + v);
+        k.y = ((off + v) << kb) | (off + u);
+      }
+      keys[i] = k;
+    }
+  }
+}
+
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortBlock = 256;  // == kRadix: one digit owner per thread
@@ -208,7 +245,7 @@ int key_bits(uint32_t n) {
 }  // namespace
 
 tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
-                    cudaStream_t st) {
+                    cudaStream_t st, const EdgeGroups* groups) {
   const uint32_t n = g->n;
   const int kb = key_bits(n);
   const uint64_t N = 2 * E;
@@ -244,9 +281,14 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
       ss.capacity = scan_scratch_entries(off_entries);
       if (cudaMalloc(&ss.sums, sizeof(unsigned long long) * ss.capacity) != cudaSuccess) { fail(TC_ERR_OOM); break; }
 
-      k_make_keys<<<grid_for(E, 256, 152 * 64), 256, 0, st>>>(d_src, d_dst, E, n, kb,
-                                                             reinterpret_cast<ulonglong2*>(keys_a),
-                                                             g->ctr); TC_LAUNCHED();
+      if (groups)
+        k_make_keys_multi<<<grid_for(E, kKeyTile, 152 * 64), 256, 0, st>>>(
+            d_src, d_dst, E, *groups, kb, reinterpret_cast<ulonglong2*>(keys_a), g->ctr);
+      else
+        k_make_keys<<<grid_for(E, 256, 152 * 64), 256, 0, st>>>(d_src, d_dst, E, n, kb,
+                                                               reinterpret_cast<ulonglong2*>(keys_a),
+                                                               g->ctr);
+      TC_LAUNCHED();
       for (int shift = 0; shift < 2 * kb && status == TC_OK; shift += kRadixBits) {
         k_radix_hist<<<(unsigned)nb, kSortBlock, 0, st>>>(keys_a, N, shift, (uint32_t)nb, hist); TC_LAUNCHED();
         if (exclusive_scan_u32(hist, hoff, hcount, ss, st) != TC_OK) { fail(TC_ERR_CUDA); break; }

@@ -142,8 +142,16 @@ tc_status exclusive_scan_u64(const unsigned long long* in, unsigned long long* o
 size_t scan_scratch_entries(uint64_t max_count);
 
 // Phases (implemented in the .cu files of the same name).
+// Several graphs' edge lists in one array: edges [ein[i], ein[i+1]) belong to
+// graph i, whose local ids must be < nvert[i] and become voff[i] + id.
+struct EdgeGroups {
+  const unsigned long long* ein;   // device, k + 1
+  const unsigned long long* voff;  // device, k + 1
+  const uint32_t* nvert;           // device, k
+  uint32_t k;
+};
 tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
-                    cudaStream_t st);
+                    cudaStream_t st, const EdgeGroups* groups = nullptr);
 tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st);
 // BFS from the k roots already stored in queue_a (all at level 0, level[] set
 // to -1 elsewhere by the caller), then the restart rule.

@@ -3,13 +3,14 @@
 A request is one graph (an edge list on the host, its vertex count and a root
 rule).
 
-- The **admission** thread takes requests in arrival order. A request is admitted while its HBM
-  footprint fits the budget next to everything already resident. The thread then builds its graph
-  on the device on its own stream (host-to-device copy and CSR build) and queues it as ready.
-- The **counting** thread takes every ready graph (up to ``max_batch``) and counts them together as
-  one batch: one concatenated CSR, one multi-source BFS, one pass of each count kernel. It then
-  answers each request and frees the graphs. The memory returns to the budget for the next
-  admissions.
+- The **admission** thread takes every request that has arrived, in arrival order and up to
+  ``max_batch``, while the requests' HBM footprints fit the budget next to everything already
+  resident. It builds them on the device as one batch on its own stream: a single
+  host-to-device copy of their edge lists, one radix sort, one concatenated CSR
+  (``tc_batch_create_from_edges``). The batch is queued as ready.
+- The **counting** thread counts ready batches one after another: one multi-source BFS and one
+  pass of each count kernel per batch. It then answers each request and frees the batch. The memory
+  returns to the budget for the next admissions.
 
 While a batch is on the device, newly arrived graphs are being admitted and built for the next one.
 Building and counting overlap; a request never waits for a fixed batch size.
@@ -111,25 +112,33 @@ class Server:
                     self.lock.wait(0.05)
                 if self.stopping and not self.pending:
                     return
-                if self.used + self.pending[0].bytes > self.budget:
-                    continue
-                req = self.pending.popleft()
-                self.used += req.bytes
+                group = []
+                while (self.pending and len(group) < self.max_batch and
+                       self.used + self.pending[0].bytes <= self.budget):
+                    req = self.pending.popleft()
+                    self.used += req.bytes
+                    group.append(req)
                 self.peak_used = max(self.peak_used, self.used)
+            if not group:
+                continue
             try:
-                g = tc.Graph(req.src, req.dst, req.n, stream=self.build_stream)
+                # one device build for the whole group: a batch straight from the edge lists
+                b = tc.Batch.from_edges([(r.src, r.dst, r.n) for r in group],
+                                        stream=self.build_stream)
                 if self.params:
-                    g.set_params(**self.params)
-                root = g.max_degree_vertex() if req.root is None else req.root
+                    b.set_params(**self.params)
+                md = b.max_degree_vertices(stream=self.build_stream)
+                roots = [md[i] if r.root is None else r.root for i, r in enumerate(group)]
                 with self.lock:
-                    self.ready.append((req, g, root))
+                    self.ready.append((group, b, roots))
                     self.lock.notify_all()
-            except Exception as e:  # the request fails alone; its memory returns
-                req.error = str(e)
-                req.done = time.perf_counter()
-                req.event.set()
+            except Exception as e:  # the group fails; its memory returns
+                now = time.perf_counter()
+                for r in group:
+                    r.error, r.done = str(e), now
+                    r.event.set()
                 with self.lock:
-                    self.used -= req.bytes
+                    self.used -= sum(r.bytes for r in group)
                     self.lock.notify_all()
 
     # -- counting -------------------------------------------------------------
@@ -140,26 +149,14 @@ class Server:
                     self.lock.wait(0.05)
                 if not self.ready and self.stopping and not self.pending:
                     return
-                take = self.ready[: self.max_batch]
-                del self.ready[: len(take)]
-            reqs = [t[0] for t in take]
-            graphs = [t[1] for t in take]
-            roots = [t[2] for t in take]
+                reqs, b, roots = self.ready.pop(0)
             try:
-                if len(graphs) == 1:
-                    counts = [graphs[0].count(roots[0], stream=self.count_stream)]
-                else:
-                    b = tc.Batch(graphs, stream=self.count_stream)
-                    if self.params:
-                        b.set_params(**self.params)
-                    counts = b.count(roots, stream=self.count_stream)
-                    b.close()
-                err = None
+                counts, err = b.count(roots, stream=self.count_stream), None
             except Exception as e:
-                counts, err = [None] * len(graphs), str(e)
+                counts, err = [None] * len(reqs), str(e)
+            b.close()
             now = time.perf_counter()
-            for r, g, c in zip(reqs, graphs, counts):
-                g.close()
+            for r, c in zip(reqs, counts):
                 r.count, r.error, r.done = c, err, now
                 r.event.set()
             with self.lock:

@@ -107,3 +107,27 @@ def test_batch_of_one_equals_single():
         b.close()
     finally:
         g.close()
+
+
+def test_batch_from_edge_lists():
+    items = mixed_graphs()
+    want, roots, levels = oracle_truth(items)
+    b = tc.Batch.from_edges([(s, d, n) for n, s, d, _ in items])
+    try:
+        md = b.max_degree_vertices()
+        for i, (n, s, d, root) in enumerate(items):
+            if root == "maxdeg":
+                assert md[i] == roots[i], i
+        assert b.count(roots) == want
+        for i, lv in enumerate(levels):
+            assert np.array_equal(b.levels(i), lv), i
+        b.set_params(small_max_degree=0, hash_chunk=64, edges_per_item=5)
+        assert b.count(roots) == want
+    finally:
+        b.close()
+    # an id beyond its own graph's size is an error even inside the union's range
+    n1, s1, d1 = graphs.complete(5)
+    with pytest.raises(tc.TCError) as ei:
+        tc.Batch.from_edges([(s1, d1, 5), (np.array([0, 7], np.uint32),
+                                             np.array([1, 2], np.uint32), 6)])
+    assert ei.value.status == 2

@@ -34,5 +34,5 @@ def test_results_alone_and_in_the_mix():
         idx = [i for i, p in enumerate(pool) if p[0] is r.src][0]
         assert r.count == alone[idx]
     assert srv.peak_used <= budget
-    assert max(srv.batches) > 1          # requests were batched together
+    assert max(srv.batches) > 1          # requests were built and counted together
     assert res["p99_ms"] >= res["p50_ms"] > 0
