@@ -170,7 +170,10 @@ typedef struct tc_params {
                                   the count fails with TC_ERR_TIMEOUT and the handle stays usable */
   uint32_t test_barrier_skip;  /* testing only: 1 makes one block leave the persistent kernel
                                   without arriving at a barrier, so the other blocks time out */
-  uint32_t reserved[3];
+  uint32_t medium_max_degree;  /* cover edges above the small bin whose larger degree is <= this
+                                  (at most 1024; 0 disables the bin) go to a warp merge: the
+                                  longer row staged in shared memory, the shorter searched in it */
+  uint32_t reserved[2];
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);

@@ -49,7 +49,8 @@ class tc_params(ctypes.Structure):
                 ("edges_per_item", ctypes.c_uint32), ("bfs_alpha", ctypes.c_uint32),
                 ("bfs_beta", ctypes.c_uint32), ("sorted_lookup", ctypes.c_uint32),
                 ("persistent_bfs", ctypes.c_uint32), ("barrier_timeout_ms", ctypes.c_uint32),
-                ("test_barrier_skip", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("test_barrier_skip", ctypes.c_uint32), ("medium_max_degree", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 _lib = None

@@ -2,6 +2,7 @@
 
 The tunables change speed only, never the count:
 - ``small_max_degree``: degree bound of the inline-merge bin;
+- ``medium_max_degree``: degree bound of the warp-merge bin;
 - ``hash_chunk``: owner-row entries per shared-memory table;
 - ``edges_per_item``: cover edges per owner-hash work item;
 - ``bfs_alpha`` / ``bfs_beta``: the direction switches of the BFS.
@@ -29,10 +30,12 @@ GRID: Dict[str, Sequence[int]] = {
     "hash_chunk": (2048, 4096, 8192, 16384),
     "edges_per_item": (64, 128, 256, 512),
     "small_max_degree": (0, 8, 16, 32, 64, 128, 256, 512, 1024),
+    "medium_max_degree": (0, 128, 256, 512, 1024),
     "bfs_alpha": (4, 15, 40),
     "bfs_beta": (8, 18, 48),
 }
-ORDER = ("hash_chunk", "edges_per_item", "small_max_degree", "bfs_alpha", "bfs_beta")
+ORDER = ("small_max_degree", "medium_max_degree", "hash_chunk", "edges_per_item", "small_max_degree",
+         "bfs_alpha", "bfs_beta")
 
 
 def signature(n: int, m: int, d_max: int, family: str = "", batch: int = 1) -> str:
@@ -60,7 +63,8 @@ def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials:
     from paper_2403_02997_gb300 import tc_params_default
     grid = dict(GRID if grid is None else grid)
     base = {k: v for k, v in tc_params_default().items()
-            if k in ("small_max_degree", "hash_chunk", "edges_per_item", "bfs_alpha", "bfs_beta")}
+            if k in ("small_max_degree", "medium_max_degree", "hash_chunk", "edges_per_item",
+                     "bfs_alpha", "bfs_beta")}
     t0 = time.time()
     best_ms, want = _measure(target, roots, base, trials)
     history = [{"params": dict(base), "ms": best_ms}]

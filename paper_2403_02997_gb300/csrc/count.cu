@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                                                        uint2* __restrict__ cover,
                                                        uint2* __restrict__ large,
                                                        uint32_t* __restrict__ ocount,
+                                                       uint32_t medium_max,
+                                                       uint2* __restrict__ medium,
                                                        const unsigned long long* __restrict__ voff,
                                                        uint32_t nb,
                                                        unsigned long long* __restrict__ gcount,
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
     const uint32_t lo = s_lo, hi = s_hi;
     for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
       const unsigned long long j = b + threadIdx.x;
-      bool is_cover = false, is_large = false;
+      bool is_cover = false, is_large = false, is_medium = false;
       uint2 ce = make_uint2(0, 0), le = make_uint2(0, 0);
       if (j < e1) {
         const uint32_t u = row_of(row_ptr, lo, hi, j);
@@ -177,6 +179,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                 }
                 run += here;
               }
+            } else if (du <= medium_max && dv <= medium_max) {
+              is_medium = true;
             } else {
               is_large = true;
               const bool v_owns = dv > du || (dv == du && v > u);
@@ -187,8 +191,77 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
         }
       }
       warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
+      warp_append_pair(is_medium, ce, medium, &ctr->num_medium);
       warp_append_pair(is_large, le, large, &ctr->num_large);
     }
+  }
+  if (run) atomicAdd(&gcount[run_g], run);
+  flush_tally(tl, ctr);
+}
+
+// Warp merge of the medium bin: one warp per cover edge {u, v} (u < v), both
+// degrees <= kMediumCap.  The longer row is staged in the warp's shared-memory
+// slice; each lane takes every 32nd id of the shorter row and binary-searches
+// it there (ids of a row ascend, so a lane's searches start where its previous
+// one ended).  A hit w counts as in Algorithm CETC-Seq: c1 when L(w) != L(u),
+// c2' when L(w) == L(u) and v < w.
+constexpr int kWarpMergeBlock = 256;
+constexpr uint32_t kMediumCap = 1024;
+
+__global__ void __launch_bounds__(kWarpMergeBlock) k_warp_merge(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, const uint2* __restrict__ medium, unsigned long long count,
+    const unsigned long long* __restrict__ voff, uint32_t nb,
+    unsigned long long* __restrict__ gcount, DevCounters* ctr) {
+  __shared__ uint32_t s_row[kWarpMergeBlock / 32][kMediumCap];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* row = s_row[warp];
+  const unsigned long long warps = (unsigned long long)gridDim.x * blockDim.x / 32;
+  Tally tl;
+  uint32_t run_g = 0xFFFFFFFFu;
+  unsigned long long run = 0;
+  for (unsigned long long e = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+       e < count; e += warps) {
+    const uint2 ed = medium[e];
+    const uint32_t u = ed.x, v = ed.y;
+    const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
+    const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
+    const bool u_long = eu - bu >= ev - bv;
+    const unsigned long long lb = u_long ? bu : bv, le = u_long ? eu : ev;
+    const unsigned long long sb = u_long ? bv : bu, se = u_long ? ev : eu;
+    const uint32_t nl = (uint32_t)(le - lb);
+    for (uint32_t j = lane; j < nl; j += 32) row[j] = col[lb + j];
+    __syncwarp();
+    const int32_t lu = level[u];
+    uint32_t lo = 0, c1 = 0, c2c = 0;
+    for (unsigned long long j = sb + lane; j < se; j += 32) {
+      const uint32_t w = col[j];
+      uint32_t a = lo, b = nl;
+      while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (row[mid] < w) a = mid + 1; else b = mid;
+      }
+      lo = a;
+      if (a < nl && row[a] == w) {
+        if (level[w] != lu) ++c1;
+        else if (v < w) ++c2c;
+      }
+    }
+    tl.c1 += c1;
+    tl.c2c += c2c;
+    if (nb) {
+      const unsigned long long here = warp_sum((unsigned long long)(c1 + c2c));
+      if (lane == 0 && here) {
+        const uint32_t gid = batch_graph_of(voff, 0, nb - 1, u);
+        if (gid != run_g) {
+          if (run) atomicAdd(&gcount[run_g], run);
+          run_g = gid;
+          run = 0;
+        }
+        run += here;
+      }
+    }
+    __syncwarp();
   }
   if (run) atomicAdd(&gcount[run_g], run);
   flush_tally(tl, ctr);
@@ -624,13 +697,21 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   const uint32_t small_max = g->params.small_max_degree;
   k_cover<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount, g->voff,
-      g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
+      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
+      g->params.medium_max_degree > kMediumCap ? kMediumCap : g->params.medium_max_degree,
+      g->medium, g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
   TC_TRY(exclusive_scan_u32(g->ocount, g->ooff, n, g->scan, st));
   TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   TC_CUDA_TRY(cudaStreamSynchronize(st));
+  const unsigned long long nmedium = g->ctr_host->num_medium;
+  if (nmedium > 0) {
+    k_warp_merge<<<grid_for(nmedium * 32, kWarpMergeBlock, sms * 16), kWarpMergeBlock, 0, st>>>(
+        g->row_ptr, g->col, g->level, g->medium, nmedium, g->voff, g->batch_k, g->gcount,
+        g->ctr); TC_LAUNCHED();
+    TC_CUDA_TRY(cudaGetLastError());
+  }
   const unsigned long long nlarge = g->ctr_host->num_large;
   if (nlarge == 0) return TC_OK;
   // level-split rows: short rows by warps, long rows in tiles

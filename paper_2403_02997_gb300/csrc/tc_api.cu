@@ -49,7 +49,7 @@ void free_graph(tc_graph* g) {
   void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
                   g->ooff,    g->ioff,  g->parent, g->fdeg,    g->ocount,  g->ofill,
                   g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums,
-                  g->lcol,    g->lsplit, g->tile_row, g->tile_cnt};
+                  g->lcol,    g->lsplit, g->tile_row, g->tile_cnt, g->medium};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -73,6 +73,7 @@ tc_status alloc_count_state(tc_graph* g) {
   TC_TRY(dalloc(&g->cover, m));
   TC_TRY(dalloc(&g->large, m));
   TC_TRY(dalloc(&g->ostream, m));
+  TC_TRY(dalloc(&g->medium, m));
   TC_TRY(dalloc(&g->lcol, g->nnz));
   TC_TRY(dalloc(&g->lsplit, n));
   // tiles of rows longer than 4096 entries, 4096 per tile: at most nnz / 2048
@@ -127,6 +128,7 @@ tc_status tc_set_params(tc_graph* g, const tc_params* p) {
   if (p->edges_per_item == 0 || p->edges_per_item > 512 || p->bfs_alpha == 0 || p->bfs_beta == 0)
     return TC_ERR_INVALID_ARG;
   if (p->barrier_timeout_ms == 0 || p->barrier_timeout_ms > 600000) return TC_ERR_INVALID_ARG;
+  if (p->medium_max_degree > 1024) return TC_ERR_INVALID_ARG;
   g->params = *p;
   return TC_OK;
 }

@@ -21,6 +21,7 @@ struct DevCounters {
   unsigned long long c2;         // apex on the same level
   unsigned long long num_cover;  // |S|
   unsigned long long num_large;  // cover edges sent to the owner-hash path
+  unsigned long long num_medium; // cover edges sent to the warp merge
   unsigned long long next_n;     // BFS: vertices discovered this step
   unsigned long long next_m;     // BFS: sum of their degrees
   unsigned long long scan_total; // total of the last device-wide scan
@@ -75,6 +76,7 @@ struct tc_graph {
   unsigned long long item_cap = 0;
   uint2* cover = nullptr;        // [m]  all cover edges (u < v)
   uint2* large = nullptr;        // [m]  (owner, streamer) of owner-hash cover edges
+  uint2* medium = nullptr;       // [m]  (u, v) cover edges of the warp-merge bin
   uint32_t* ostream = nullptr;   // [m]  streamers bucketed by owner
   uint32_t* lcol = nullptr;      // [nnz] rows reordered [other-level | same-level] per count
   unsigned long long* lsplit = nullptr;  // [n] start of the same-level part of each row

@@ -31,7 +31,8 @@ class FakeTarget:
 def defaults(monkeypatch):
     import paper_2403_02997_gb300 as tc
     monkeypatch.setattr(tc, "tc_params_default",
-                        lambda: dict(small_max_degree=32, hash_chunk=8192, edges_per_item=512,
+                        lambda: dict(small_max_degree=32, medium_max_degree=0, hash_chunk=8192,
+                                     edges_per_item=512,
                                      bfs_alpha=15, bfs_beta=18, sorted_lookup=0))
 
 

@@ -29,6 +29,8 @@ PARAMS = {
     "tiny_chunks": dict(small_max_degree=0, hash_chunk=32, edges_per_item=3),
     "chunk64_slice1": dict(small_max_degree=2, hash_chunk=64, edges_per_item=1),
     "sorted_lookup": dict(small_max_degree=0, hash_chunk=128, edges_per_item=7, sorted_lookup=1),
+    "medium_bin": dict(small_max_degree=4, medium_max_degree=1024),
+    "medium_only": dict(small_max_degree=0, medium_max_degree=1024, hash_chunk=64),
 }
 
 
