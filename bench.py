@@ -37,7 +37,8 @@ from paper_2403_02997_gb300 import gen  # noqa: E402
 
 WORKLOADS = {"rmat24": gen.RMAT_24, "er1024": gen.ER_1024, "mesh4096": gen.MESH_4096,
              # smaller cases of the same family, for profiling captures
-             "rmat21": gen.rmat_spec(21, 16, 2), "rmat16": gen.rmat_spec(16, 16, 2)}
+             "rmat21": gen.rmat_spec(21, 16, 2), "rmat23": gen.rmat_spec(23, 16, 2),
+             "rmat16": gen.rmat_spec(16, 16, 2)}
 METRIC = "input edges/s (exact triangle count, tc_count on device-resident CSR)"
 L2_BYTES = 129 * 2**20
 

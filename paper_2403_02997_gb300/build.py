@@ -20,6 +20,8 @@ LIB = os.path.join(HERE, "libtc.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]
+# extra nvcc flags (e.g. -D defines for kernel variants), from the environment
+FLAGS += os.environ.get("TC_NVCC_FLAGS", "").split()
 
 
 def sources():
@@ -32,7 +34,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("TC_NVCC_FLAGS"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
