@@ -26,10 +26,10 @@
 // k_owner_hash   one CTA per work item (owner h, slice of h's cover edges):
 //                N(h) is taken in chunks; each chunk goes into a shared-memory
 //                hash table (the scatter / probe scheme of Algorithm EHP; two-
-//                choice cuckoo buckets of 4 behind a one-bit-per-slot filter:
-//                a miss costs one 4-byte load, a hit two 16-byte loads), and
-//                every edge {h, x} of the slice streams its segments of N(x) up
-//                to the chunk's largest id through it.
+//                table cuckoo hashing, one slot per bucket: every lookup is two
+//                4-byte loads, hit or miss), and every edge {h, x} of the slice
+//                streams its segments of N(x), 128 ids per warp step, up to the
+//                chunk's largest id through it.
 // Per-thread counts are reduced by warp shuffles and one atomic per CTA.
 #include "tc_internal.cuh"
 
@@ -41,14 +41,12 @@ constexpr int kCoverBlock = 256;
 constexpr int kCoverEntriesPerBlock = 2048;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kHashBlock = 512;
-constexpr int kStreamUnroll = 4;
 constexpr int kMaxEdgesPerItem = 512;
 constexpr uint32_t kSplitMax = 4096;    // rows longer than this are split in tiles
 constexpr uint32_t kSplitTile = 4096;   // entries per tile of a long row
 constexpr int kTileBlock = 512;         // threads per tile block (8 entries each)
 constexpr uint32_t kHashA = 2654435761u;  // multiplicative hashing constants (odd)
 constexpr uint32_t kHashB = 0x85EBCA77u;
-constexpr uint32_t kHashC = 0xC2B2AE35u;
 constexpr int kCuckooRounds = 96;
 
 __device__ __forceinline__ void warp_append_pair(bool take, uint2 value, uint2* list,
@@ -431,119 +429,106 @@ __global__ void k_item_owner(const unsigned long long* __restrict__ ioff, uint32
 
 // ---- the owner-hash kernel ----------------------------------------------
 
-// Two-choice cuckoo hashing with buckets of 4 slots in shared memory, behind a
-// bitmap filter of 16 bits per entry (one hash; a miss is rejected by one load
-// with probability about 15/16).
+// Shared memory of k_owner_hash: the chunk's hash tables (or its sorted copy).
+extern __shared__ uint32_t s_table[];
+
+// Cuckoo hashing with two tables of one slot per bucket: an id w sits either
+// at T1[h1(w)] or at T2[h2(w)] (T1 = s_table[0, size), T2 = s_table[size,
+// 2 size)), so a lookup is two 4-byte shared loads and two compares, the same
+// instructions for a hit and a miss (no divergence inside the warp).  Each
+// table has `size` >= 5/4 x entries slots (load <= 0.4, below the 1/2
+// threshold of two-table cuckoo hashing); indices are multiplicative hashes
+// reduced to [0, size) by a high multiply.
 struct Cuckoo {
-  uint32_t* table;   // 4 * 2^(32 - shift) slots
-  uint32_t* filter;  // 2^(32 - fshift) bits
-  uint32_t shift;    // 32 - log2(buckets)
-  uint32_t fshift;   // 32 - log2(filter bits)
-  __device__ __forceinline__ uint32_t b1(uint32_t w) const { return (w * kHashA) >> shift; }
-  __device__ __forceinline__ uint32_t b2(uint32_t w) const {
-    const uint32_t a = (w * kHashA) >> shift, b = (w * kHashB) >> shift;
-    return a == b ? (b ^ 1u) : b;
+  uint32_t size;
+  __device__ __forceinline__ uint32_t h1(uint32_t w) const { return __umulhi(w * kHashA, size); }
+  __device__ __forceinline__ uint32_t h2(uint32_t w) const {
+    return size + __umulhi(w * kHashB, size);
   }
-  __device__ __forceinline__ uint32_t fbit(uint32_t w) const { return (w * kHashC) >> fshift; }
   // Insert w; false if it could not be placed (the caller falls back).
-  __device__ __forceinline__ bool insert(uint32_t w, unsigned salt) const {
-    const uint32_t f = fbit(w);
-    atomicOr(&filter[f >> 5], 1u << (f & 31));
+  __device__ __forceinline__ bool insert(uint32_t w) const {
     uint32_t cur = w;
     for (int it = 0; it < kCuckooRounds; ++it) {
-      const uint32_t a = b1(cur), b = b2(cur);
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        uint32_t* slot = &table[4 * (t < 4 ? a : b) + (t & 3)];
-        if (*slot == kEmpty && atomicCAS(slot, kEmpty, cur) == kEmpty) return true;
-      }
-      const uint32_t victim = ((it + salt) & 1) ? b : a;
-      cur = atomicExch(&table[4 * victim + ((it * 5u + salt) & 3u)], cur);
+      uint32_t* s1 = &s_table[h1(cur)];
+      if (*s1 == kEmpty && atomicCAS(s1, kEmpty, cur) == kEmpty) return true;
+      uint32_t* s2 = &s_table[h2(cur)];
+      if (*s2 == kEmpty && atomicCAS(s2, kEmpty, cur) == kEmpty) return true;
+      cur = atomicExch((it & 1) ? s2 : s1, cur);  // evict; the evicted id moves on
       if (cur == kEmpty) return true;
     }
     return false;
   }
-  __device__ __forceinline__ bool contains(uint32_t w) const {
-    const uint32_t f = fbit(w);
-    if (!((filter[f >> 5] >> (f & 31)) & 1u)) return false;
-    const uint4 p = reinterpret_cast<const uint4*>(table)[b1(w)];
-    const uint4 q = reinterpret_cast<const uint4*>(table)[b2(w)];
-    return (p.x == w) | (p.y == w) | (p.z == w) | (p.w == w) | (q.x == w) | (q.y == w) |
-           (q.z == w) | (q.w == w);
+  __device__ __forceinline__ uint32_t contains(uint32_t w) const {
+    return (uint32_t)((s_table[h1(w)] == w) | (s_table[h2(w)] == w));
   }
 };
 
-// Sorted-array lookup, used for a chunk whose cuckoo build failed.
-__device__ __forceinline__ bool sorted_contains(const uint32_t* a, uint32_t len, uint32_t w) {
+// Sorted-array lookup in s_table[0, len), used for a chunk whose cuckoo build
+// failed.
+__device__ __forceinline__ uint32_t sorted_contains(uint32_t len, uint32_t w) {
   uint32_t lo = 0, hi = len;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < w) lo = mid + 1; else hi = mid;
+    if (s_table[mid] < w) lo = mid + 1; else hi = mid;
   }
-  return lo < len && a[lo] == w;
-}
-
-__device__ __forceinline__ void load_block(const uint32_t* __restrict__ arr, unsigned long long cur,
-                                           unsigned long long end, uint32_t (&w)[kStreamUnroll]) {
-  const unsigned lane = lane_id();
-  const unsigned long long left = end - cur;
-  const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
-#pragma unroll
-  for (int u = 0; u < kStreamUnroll; ++u) {
-    const uint32_t j = lane + 32u * u;
-    w[u] = j < rem ? __ldg(arr + cur + j) : kEmpty;
-  }
+  return lo < len && s_table[lo] == w;
 }
 
 // Lookup of one streamed id in the chunk: the cuckoo table, or for a chunk
 // whose table could not be built, the sorted copy.
 template <bool kSorted>
 __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_len, uint32_t w) {
-  if (kSorted) return sorted_contains(ck.table, sorted_len, w);
+  if (kSorted) return sorted_contains(sorted_len, w);
   return ck.contains(w);
 }
 
 // The warp streams arr[cur, end) up to the first id above hi (kBounded; the
 // last chunk of a row is unbounded), looking every element up in the chunk;
-// returns the new cursor and adds the hits.  Blocks of kStreamUnroll x 32
-// elements; the next block is loaded before the current one is looked up --
-// in a bounded pass only while the current block ends at or below hi, so a
-// pass reads at most one block past its part (re-read by the next chunk).
+// returns the new cursor and adds the hits.  One step is 128 ids: lane l holds
+// ids l, l + 32, l + 64 and l + 96 of the step (coalesced loads).  The next
+// step is loaded before the current one is looked up -- in a bounded pass only
+// while the current step ends at or below hi, so a pass reads at most one step
+// past its part (read again by the next chunk).  In the last step, whole rows
+// of 32 ids past end or above hi are skipped and the rest is masked per id.  A
+// segment is one row's part: shorter than 2^32.
 template <bool kBounded, bool kSorted>
 __device__ __forceinline__ unsigned long long stream_segment(
-    const uint32_t* __restrict__ arr, unsigned long long cur, const unsigned long long end,
+    const uint32_t* __restrict__ arr, const unsigned long long cur, const unsigned long long end,
     const uint32_t hi, const Cuckoo& ck, const uint32_t sorted_len, uint32_t& hits) {
   if (cur >= end) return end;
-  const unsigned lane = lane_id();
-  uint32_t w[kStreamUnroll];
-  load_block(arr, cur, end, w);
+  const uint32_t lane = lane_id();
+  const uint32_t* p = arr + cur + lane;
+  uint32_t len = (uint32_t)(end - cur) - lane;  // ids from p to end (as int: may be <= 0)
+  uint32_t w[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) w[t] = (int)len > 32 * t ? __ldg(p + 32 * t) : kEmpty;
   for (;;) {
-    const unsigned long long next = cur + 32ull * kStreamUnroll;
-    bool more = next < end;
-    if (kBounded) more = more && __shfl_sync(0xffffffffu, w[kStreamUnroll - 1], 31) <= hi;
-    uint32_t wn[kStreamUnroll];
-    if (more) load_block(arr, next, end, wn);
+    bool more = (int)(len + lane) > 128;
+    if (kBounded) more = more && __shfl_sync(0xffffffffu, w[3], 31) <= hi;
+    uint32_t wn[4];
     if (more) {
 #pragma unroll
-      for (int u = 0; u < kStreamUnroll; ++u) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
+      for (int t = 0; t < 4; ++t) wn[t] = (int)len > 128 + 32 * t ? __ldg(p + 128 + 32 * t) : kEmpty;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) hits += chunk_hit<kSorted>(ck, sorted_len, w[t]);
     } else {
-      const unsigned long long left = end - cur;
-      const uint32_t rem = left > 0x40000000ull ? 0x40000000u : (uint32_t)left;
+      uint32_t taken = 0;
 #pragma unroll
-      for (int u = 0; u < kStreamUnroll; ++u) {
-        const uint32_t j = lane + 32u * u;
-        const bool in = j < rem && (!kBounded || w[u] <= hi);
-        const unsigned stop = __ballot_sync(0xffffffffu, !in);
-        const uint32_t take = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
-        if (lane < take) hits += chunk_hit<kSorted>(ck, sorted_len, w[u]);
-        if (stop) return cur + 32ull * u + take;
+      for (int t = 0; t < 4; ++t) {
+        if ((int)(len + lane) <= 32 * t) break;                              // past end
+        if (kBounded && __shfl_sync(0xffffffffu, w[t], 0) > hi) break;       // above hi
+        const bool in = (int)len > 32 * t && (!kBounded || w[t] <= hi);
+        taken += in;
+        if (in) hits += chunk_hit<kSorted>(ck, sorted_len, w[t]);
       }
-      // the whole block was in range; it was the last one of the segment
-      return end;
+      // the ids taken are a prefix of the step: the new cursor follows them
+      taken = __reduce_add_sync(0xffffffffu, taken);
+      return (unsigned long long)(p - lane - arr) + taken;
     }
-    cur = next;
+    p += 128;
+    len -= 128;
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) w[u] = wn[u];
+    for (int t = 0; t < 4; ++t) w[t] = wn[t];
   }
 }
 
@@ -554,8 +539,25 @@ __device__ __forceinline__ void stream_edge(const uint32_t* __restrict__ lcol,
                                             unsigned long long& b, unsigned long long be,
                                             uint32_t hi, const Cuckoo& ck, uint32_t sorted_len,
                                             uint32_t& c1, uint32_t& c2c) {
-  a = stream_segment<kBounded, kSorted>(lcol, a, ae, hi, ck, sorted_len, c1);
-  b = stream_segment<kBounded, kSorted>(lcol, b, be, hi, ck, sorted_len, c2c);
+  constexpr unsigned long long kPiece = 1ull << 30;  // stream_segment takes < 2^31 ids
+#pragma unroll 1
+  for (int part = 0; part < 2; ++part) {  // one copy of the loop for both segments
+    unsigned long long cur = part ? b : a;
+    const unsigned long long end = part ? be : ae;
+    uint32_t hits = 0;
+    for (;;) {
+      const unsigned long long e = end - cur > kPiece ? cur + kPiece : end;
+      cur = stream_segment<kBounded, kSorted>(lcol, cur, e, hi, ck, sorted_len, hits);
+      if (cur < e || e == end) break;
+    }
+    if (part) {
+      b = cur;
+      c2c += hits;
+    } else {
+      a = cur;
+      c1 += hits;
+    }
+  }
 }
 
 // The rare path (a chunk kept as a sorted array), out of line so it does not
@@ -587,7 +589,7 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // chunk's largest id (rows are sorted: cursors only move forward, and each
 // streamed element is looked up in exactly one chunk; the last chunk takes the
 // rest).  Warps take edges one at a time from a shared counter.
-__global__ void __launch_bounds__(kHashBlock) k_owner_hash(
+__global__ void __launch_bounds__(kHashBlock, 2) k_owner_hash(
     const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
     const uint32_t* __restrict__ lcol, const unsigned long long* __restrict__ lsplit,
     const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
@@ -595,13 +597,10 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
     unsigned long long nitems, uint32_t chunk, uint32_t per_item, uint32_t force_sorted,
     const unsigned long long* __restrict__ voff, uint32_t nb,
     unsigned long long* __restrict__ gcount, DevCounters* ctr) {
-  extern __shared__ uint4 table4[];
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
   __shared__ unsigned long long s_a[kMaxEdgesPerItem], s_ae[kMaxEdgesPerItem];
   __shared__ unsigned long long s_b[kMaxEdgesPerItem], s_be[kMaxEdgesPerItem];
-  uint32_t* table = reinterpret_cast<uint32_t*>(table4);
-  uint32_t* filter = table + 2 * chunk;
   const unsigned lane = lane_id();
   Tally tl;
   for (;;) {
@@ -630,14 +629,10 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
       const uint32_t entries = (uint32_t)(ce - cb);
       const bool bounded = c + 1 < chunks;
       const uint32_t hi_id = bounded ? col[ce - 1] : kEmpty;
-      // buckets: a power of two >= entries / 2 (4 slots each: load <= 1/2), >= 16;
-      // filter: a power of two >= 16 bits per entry, >= 1024 bits
-      uint32_t bbits = 4, fbits = 10;
-      while ((4u << bbits) < 2 * entries) ++bbits;
-      while ((1u << fbits) < 16 * entries) ++fbits;
-      const Cuckoo ck{table, filter, 32u - bbits, 32u - fbits};
-      for (uint32_t i = threadIdx.x; i < (4u << bbits); i += blockDim.x) table[i] = kEmpty;
-      for (uint32_t i = threadIdx.x; i < (1u << (fbits - 5)); i += blockDim.x) filter[i] = 0u;
+      // two tables of >= 5/4 x entries slots each (load <= 0.4)
+      const uint32_t size = entries + entries / 4 + 1;
+      const Cuckoo ck{size};
+      for (uint32_t i = threadIdx.x; i < 2 * size; i += blockDim.x) s_table[i] = kEmpty;
       if (threadIdx.x == 0) {
         s_next = 0;
         s_fail = force_sorted;
@@ -645,11 +640,11 @@ __global__ void __launch_bounds__(kHashBlock) k_owner_hash(
       __syncthreads();
       if (!force_sorted)
         for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x)
-          if (!ck.insert(col[j], threadIdx.x)) s_fail = 1;
+          if (!ck.insert(col[j])) s_fail = 1;
       __syncthreads();
       const bool sorted = s_fail != 0;
       if (sorted) {  // rare: keep the chunk as a sorted array instead
-        for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) table[i] = col[cb + i];
+        for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_table[i] = col[cb + i];
         __syncthreads();
       }
       for (;;) {
@@ -757,8 +752,8 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
     g->item_cap = want;
   }
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
-  // table: 2 * chunk slots (buckets of 4, load <= 1/2) + filter: 16 bits per entry
-  const size_t smem = sizeof(uint32_t) * (2 * (size_t)chunk + (size_t)chunk / 2 + 32);
+  // two cuckoo tables of chunk + chunk / 4 + 1 slots
+  const size_t smem = sizeof(uint32_t) * 2 * ((size_t)chunk + chunk / 4 + 1);
   TC_CUDA_TRY(cudaFuncSetAttribute(k_owner_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   int per_sm = 0;
