@@ -159,7 +159,7 @@ tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v);
 typedef struct tc_params {
   uint32_t small_max_degree; /* cover edges with both degrees <= this use the direct merge */
   uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (power of 2, 32..16384) */
-  uint32_t edges_per_item;   /* cover edges per hash work item (1..512) */
+  uint32_t edges_per_item;   /* cover edges per hash work item (1..hash_block) */
   uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
   uint32_t sorted_lookup;    /* 1: look ids up by binary search in the sorted chunk instead of
@@ -173,7 +173,9 @@ typedef struct tc_params {
   uint32_t medium_max_degree;  /* cover edges above the small bin whose larger degree is <= this
                                   (at most 1024; 0 disables the bin) go to a warp merge: the
                                   longer row staged in shared memory, the shorter searched in it */
-  uint32_t reserved[2];
+  uint32_t hash_block;       /* threads per owner-hash block: 512 (default) or 1024 (one block per
+                                SM; allows hash_chunk 16384 with the SM's full warp count) */
+  uint32_t reserved[1];
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);

@@ -50,7 +50,7 @@ class tc_params(ctypes.Structure):
                 ("bfs_beta", ctypes.c_uint32), ("sorted_lookup", ctypes.c_uint32),
                 ("persistent_bfs", ctypes.c_uint32), ("barrier_timeout_ms", ctypes.c_uint32),
                 ("test_barrier_skip", ctypes.c_uint32), ("medium_max_degree", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("hash_block", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 _lib = None

@@ -3,6 +3,7 @@
 The tunables change speed only, never the count:
 - ``small_max_degree``: degree bound of the inline-merge bin;
 - ``medium_max_degree``: degree bound of the warp-merge bin;
+- ``hash_block``: threads per owner-hash block (512, or 1024 with one block per SM);
 - ``hash_chunk``: owner-row entries per shared-memory table;
 - ``edges_per_item``: cover edges per owner-hash work item;
 - ``bfs_alpha`` / ``bfs_beta``: the direction switches of the BFS.
@@ -27,15 +28,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuned_params.json")
 
 GRID: Dict[str, Sequence[int]] = {
+    "hash_block": (512, 1024),
     "hash_chunk": (2048, 4096, 8192, 16384),
-    "edges_per_item": (64, 128, 256, 512),
+    "edges_per_item": (64, 128, 256, 512, 1024),
     "small_max_degree": (0, 8, 16, 32, 64, 128, 256, 512, 1024),
     "medium_max_degree": (0, 128, 256, 512, 1024),
     "bfs_alpha": (4, 15, 40),
     "bfs_beta": (8, 18, 48),
 }
-ORDER = ("small_max_degree", "medium_max_degree", "hash_chunk", "edges_per_item", "small_max_degree",
-         "bfs_alpha", "bfs_beta")
+ORDER = ("small_max_degree", "medium_max_degree", "hash_block", "hash_chunk", "edges_per_item",
+         "small_max_degree", "bfs_alpha", "bfs_beta")
 
 
 def signature(n: int, m: int, d_max: int, family: str = "", batch: int = 1) -> str:
@@ -63,14 +65,14 @@ def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials:
     from paper_2403_02997_gb300 import tc_params_default
     grid = dict(GRID if grid is None else grid)
     base = {k: v for k, v in tc_params_default().items()
-            if k in ("small_max_degree", "medium_max_degree", "hash_chunk", "edges_per_item",
-                     "bfs_alpha", "bfs_beta")}
+            if k in ("small_max_degree", "medium_max_degree", "hash_block", "hash_chunk",
+                     "edges_per_item", "bfs_alpha", "bfs_beta")}
     t0 = time.time()
     best_ms, want = _measure(target, roots, base, trials)
     history = [{"params": dict(base), "ms": best_ms}]
     cur = dict(base)
     for name in ORDER:
-        if name not in grid:
+        if name not in grid or name not in cur:  # not a tunable of this library
             continue
         for val in grid[name]:
             if val == cur[name] or time.time() - t0 > time_budget_s:

@@ -40,8 +40,7 @@ namespace {
 constexpr int kCoverBlock = 256;
 constexpr int kCoverEntriesPerBlock = 2048;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr int kHashBlock = 512;
-constexpr int kMaxEdgesPerItem = 512;
+constexpr int kHashBlock = 512;         // threads of an owner-hash block (or 2x, see hash_block)
 constexpr uint32_t kSplitMax = 4096;    // rows longer than this are split in tiles
 constexpr uint32_t kSplitTile = 4096;   // entries per tile of a long row
 constexpr int kTileBlock = 512;         // threads per tile block (8 entries each)
@@ -477,7 +476,7 @@ __device__ __forceinline__ uint32_t sorted_contains(uint32_t len, uint32_t w) {
 // Lookup of one streamed id in the chunk: the cuckoo table, or for a chunk
 // whose table could not be built, the sorted copy.
 template <bool kSorted>
-__device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_len, uint32_t w) {
+__device__ __forceinline__ uint32_t chunk_hit(const Cuckoo ck, uint32_t sorted_len, uint32_t w) {
   if (kSorted) return sorted_contains(sorted_len, w);
   return ck.contains(w);
 }
@@ -490,11 +489,11 @@ __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo& ck, uint32_t sorted_
 // while the current step ends at or below hi, so a pass reads at most one step
 // past its part (read again by the next chunk).  In the last step, whole rows
 // of 32 ids past end or above hi are skipped and the rest is masked per id.  A
-// segment is one row's part: shorter than 2^32.
+// segment is one row's part: shorter than n < 2^31.
 template <bool kBounded, bool kSorted>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, const unsigned long long cur, const unsigned long long end,
-    const uint32_t hi, const Cuckoo& ck, const uint32_t sorted_len, uint32_t& hits) {
+    const uint32_t hi, const Cuckoo ck, const uint32_t sorted_len, uint32_t& hits) {
   if (cur >= end) return end;
   const uint32_t lane = lane_id();
   const uint32_t* p = arr + cur + lane;
@@ -512,17 +511,18 @@ __device__ __forceinline__ unsigned long long stream_segment(
 #pragma unroll
       for (int t = 0; t < 4; ++t) hits += chunk_hit<kSorted>(ck, sorted_len, w[t]);
     } else {
+      // ids ascend with 32 t + lane, so the ids taken (before end, at most hi)
+      // form a prefix of the step: stop at the first row of 32 with none
       uint32_t taken = 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if ((int)(len + lane) <= 32 * t) break;                              // past end
-        if (kBounded && __shfl_sync(0xffffffffu, w[t], 0) > hi) break;       // above hi
         const bool in = (int)len > 32 * t && (!kBounded || w[t] <= hi);
-        taken += in;
-        if (in) hits += chunk_hit<kSorted>(ck, sorted_len, w[t]);
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (!m) break;
+        taken += __popc(m);
+        hits += (uint32_t)in & chunk_hit<kSorted>(ck, sorted_len, w[t]);
       }
-      // the ids taken are a prefix of the step: the new cursor follows them
-      taken = __reduce_add_sync(0xffffffffu, taken);
+      // the new cursor follows the ids taken
       return (unsigned long long)(p - lane - arr) + taken;
     }
     p += 128;
@@ -532,43 +532,49 @@ __device__ __forceinline__ unsigned long long stream_segment(
   }
 }
 
-// Both segments of one cover edge for one chunk; returns the new cursors.
+// Cursors and hits of one cover edge after a chunk.
+struct EdgePass {
+  unsigned long long a, b;  // cursors of the other-level and same-level segments
+  uint32_t c1, c2c;         // hits in each
+};
+
+// Both segments of one cover edge for one chunk.  A segment is part of one row,
+// so it holds fewer than n < 2^31 ids (stream_segment's length is an int).
 template <bool kBounded, bool kSorted>
-__device__ __forceinline__ void stream_edge(const uint32_t* __restrict__ lcol,
-                                            unsigned long long& a, unsigned long long ae,
-                                            unsigned long long& b, unsigned long long be,
-                                            uint32_t hi, const Cuckoo& ck, uint32_t sorted_len,
-                                            uint32_t& c1, uint32_t& c2c) {
-  constexpr unsigned long long kPiece = 1ull << 30;  // stream_segment takes < 2^31 ids
+__device__ __forceinline__ EdgePass stream_edge(const uint32_t* __restrict__ lcol,
+                                                unsigned long long a, unsigned long long ae,
+                                                unsigned long long b, unsigned long long be,
+                                                uint32_t hi, const Cuckoo ck,
+                                                uint32_t sorted_len) {
+  EdgePass r{a, b, 0, 0};
 #pragma unroll 1
   for (int part = 0; part < 2; ++part) {  // one copy of the loop for both segments
-    unsigned long long cur = part ? b : a;
-    const unsigned long long end = part ? be : ae;
     uint32_t hits = 0;
-    for (;;) {
-      const unsigned long long e = end - cur > kPiece ? cur + kPiece : end;
-      cur = stream_segment<kBounded, kSorted>(lcol, cur, e, hi, ck, sorted_len, hits);
-      if (cur < e || e == end) break;
-    }
+    const unsigned long long cur = stream_segment<kBounded, kSorted>(
+        lcol, part ? b : a, part ? be : ae, hi, ck, sorted_len, hits);
     if (part) {
-      b = cur;
-      c2c += hits;
+      r.b = cur;
+      r.c2c = hits;
     } else {
-      a = cur;
-      c1 += hits;
+      r.a = cur;
+      r.c1 = hits;
     }
   }
+  return r;
 }
 
 // The rare path (a chunk kept as a sorted array), out of line so it does not
-// weigh on the registers of the hot loop.
-__device__ __noinline__ void stream_edge_sorted(const uint32_t* __restrict__ lcol,
-                                                unsigned long long& a, unsigned long long ae,
-                                                unsigned long long& b, unsigned long long be,
-                                                bool bounded, uint32_t hi, const Cuckoo& ck,
-                                                uint32_t sorted_len, uint32_t& c1, uint32_t& c2c) {
-  if (bounded) stream_edge<true, true>(lcol, a, ae, b, be, hi, ck, sorted_len, c1, c2c);
-  else stream_edge<false, true>(lcol, a, ae, b, be, hi, ck, sorted_len, c1, c2c);
+// weigh on the registers of the hot loop.  Arguments and result go by value:
+// nothing of the caller's has its address taken (which would put it in local
+// memory).
+__device__ __noinline__ EdgePass stream_edge_sorted(const uint32_t* __restrict__ lcol,
+                                                    unsigned long long a, unsigned long long ae,
+                                                    unsigned long long b, unsigned long long be,
+                                                    bool bounded, uint32_t hi,
+                                                    uint32_t sorted_len) {
+  const Cuckoo none{0};
+  if (bounded) return stream_edge<true, true>(lcol, a, ae, b, be, hi, none, sorted_len);
+  return stream_edge<false, true>(lcol, a, ae, b, be, hi, none, sorted_len);
 }
 
 // First index in arr[a, b) (sorted) with arr[i] >= t.
@@ -589,7 +595,8 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // chunk's largest id (rows are sorted: cursors only move forward, and each
 // streamed element is looked up in exactly one chunk; the last chunk takes the
 // rest).  Warps take edges one at a time from a shared counter.
-__global__ void __launch_bounds__(kHashBlock, 2) k_owner_hash(
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
     const uint32_t* __restrict__ lcol, const unsigned long long* __restrict__ lsplit,
     const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
@@ -599,8 +606,9 @@ __global__ void __launch_bounds__(kHashBlock, 2) k_owner_hash(
     unsigned long long* __restrict__ gcount, DevCounters* ctr) {
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
-  __shared__ unsigned long long s_a[kMaxEdgesPerItem], s_ae[kMaxEdgesPerItem];
-  __shared__ unsigned long long s_b[kMaxEdgesPerItem], s_be[kMaxEdgesPerItem];
+  // cursors of the slice's edges (edges_per_item <= kThreads)
+  __shared__ unsigned long long s_a[kThreads], s_ae[kThreads];
+  __shared__ unsigned long long s_b[kThreads], s_be[kThreads];
   const unsigned lane = lane_id();
   Tally tl;
   for (;;) {
@@ -652,19 +660,20 @@ __global__ void __launch_bounds__(kHashBlock, 2) k_owner_hash(
         if (lane == 0) i = atomicAdd(&s_next, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= ne) break;
-        uint32_t c1 = 0, c2c = 0;
-        unsigned long long a = s_a[i], b = s_b[i];
+        const unsigned long long a = s_a[i], b = s_b[i];
         const unsigned long long ae = s_ae[i], be = s_be[i];
+        EdgePass r;
         if (!sorted) {
-          if (bounded) stream_edge<true, false>(lcol, a, ae, b, be, hi_id, ck, entries, c1, c2c);
-          else stream_edge<false, false>(lcol, a, ae, b, be, hi_id, ck, entries, c1, c2c);
+          if (bounded) r = stream_edge<true, false>(lcol, a, ae, b, be, hi_id, ck, entries);
+          else r = stream_edge<false, false>(lcol, a, ae, b, be, hi_id, ck, entries);
         } else {
-          stream_edge_sorted(lcol, a, ae, b, be, bounded, hi_id, ck, entries, c1, c2c);
+          r = stream_edge_sorted(lcol, a, ae, b, be, bounded, hi_id, entries);
         }
         if (lane == 0) {
-          s_a[i] = a;
-          s_b[i] = b;
+          s_a[i] = r.a;
+          s_b[i] = r.b;
         }
+        const uint32_t c1 = r.c1, c2c = r.c2c;
         tl.c1 += c1;
         tl.c2c += c2c;
         item_hits += c1 + c2c;
@@ -754,18 +763,27 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
   // two cuckoo tables of chunk + chunk / 4 + 1 slots
   const size_t smem = sizeof(uint32_t) * 2 * ((size_t)chunk + chunk / 4 + 1);
-  TC_CUDA_TRY(cudaFuncSetAttribute(k_owner_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  const bool wide = g->params.hash_block == 2 * kHashBlock;
+  const int threads = wide ? 2 * kHashBlock : kHashBlock;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock>
+                          : (const void*)k_owner_hash<kHashBlock>;
+  TC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_owner_hash, kHashBlock, smem));
+  TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   if (per_sm < 1) per_sm = 1;
   unsigned grid = (unsigned)(sms * per_sm);
   if (nitems < grid) grid = (unsigned)nitems;
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
-  k_owner_hash<<<grid, kHashBlock, smem, st>>>(g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff,
-                                              g->ostream, g->ioff, g->item_owner, nitems, chunk,
-                                              per_item, g->params.sorted_lookup ? 1u : 0u,
-                                              g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
+  const uint32_t force_sorted = g->params.sorted_lookup ? 1u : 0u;
+  if (wide)
+    k_owner_hash<2 * kHashBlock><<<grid, threads, smem, st>>>(
+        g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff, g->ostream, g->ioff, g->item_owner,
+        nitems, chunk, per_item, force_sorted, g->voff, g->batch_k, g->gcount, g->ctr);
+  else
+    k_owner_hash<kHashBlock><<<grid, threads, smem, st>>>(
+        g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff, g->ostream, g->ioff, g->item_owner,
+        nitems, chunk, per_item, force_sorted, g->voff, g->batch_k, g->gcount, g->ctr);
+  TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

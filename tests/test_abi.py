@@ -54,6 +54,7 @@ def test_host_side_argument_checks(lib):
     p = tc.tc_params()
     assert lib.tc_params_default(ctypes.byref(p)) == 0
     assert p.hash_chunk & (p.hash_chunk - 1) == 0
+    assert p.hash_block == 512 and p.edges_per_item <= p.hash_block
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

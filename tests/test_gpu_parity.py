@@ -4,7 +4,7 @@ Counts, c1 / c2, BFS levels, the cover-edge set and the CSR are integers and
 must be bit-exact.  The cover set has no defined order on the device, so both
 sides are compared sorted.  Parameter sets steer every cover edge through each
 intersection kernel: the direct merge, the owner hash with one chunk, and the
-owner hash with many chunks and many slices.
+owner hash with many chunks and many slices, with 512- and 1024-thread blocks.
 """
 import json
 import os
@@ -31,6 +31,8 @@ PARAMS = {
     "sorted_lookup": dict(small_max_degree=0, hash_chunk=128, edges_per_item=7, sorted_lookup=1),
     "medium_bin": dict(small_max_degree=4, medium_max_degree=1024),
     "medium_only": dict(small_max_degree=0, medium_max_degree=1024, hash_chunk=64),
+    "block1024": dict(small_max_degree=0, hash_block=1024, hash_chunk=16384, edges_per_item=1024),
+    "block1024_tiny": dict(small_max_degree=0, hash_block=1024, hash_chunk=32, edges_per_item=5),
 }
 
 
