@@ -158,7 +158,8 @@ tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v);
  */
 typedef struct tc_params {
   uint32_t small_max_degree; /* cover edges with both degrees <= this use the direct merge */
-  uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (power of 2, 32..16384) */
+  uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (multiple of 32,
+                                32..16384) */
   uint32_t edges_per_item;   /* cover edges per hash work item (1..hash_block) */
   uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
@@ -179,6 +180,8 @@ typedef struct tc_params {
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);
+/* Errors: TC_ERR_INVALID_ARG for a value out of range, or for a hash_chunk
+ * whose tables exceed the device's shared memory per block. */
 tc_status tc_set_params(tc_graph* g, const tc_params* p);
 
 /*

@@ -431,6 +431,12 @@ __global__ void k_item_owner(const unsigned long long* __restrict__ ioff, uint32
 // Shared memory of k_owner_hash: the chunk's hash tables (or its sorted copy).
 extern __shared__ uint32_t s_table[];
 
+// Dynamic shared memory of k_owner_hash for chunks of up to `chunk` entries:
+// two cuckoo tables of chunk + chunk / 4 + 1 slots.
+__host__ __device__ constexpr size_t owner_hash_smem(uint32_t chunk) {
+  return sizeof(uint32_t) * 2 * ((size_t)chunk + chunk / 4 + 1);
+}
+
 // Cuckoo hashing with two tables of one slot per bucket: an id w sits either
 // at T1[h1(w)] or at T2[h2(w)] (T1 = s_table[0, size), T2 = s_table[size,
 // 2 size)), so a lookup is two 4-byte shared loads and two compares, the same
@@ -690,6 +696,19 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
 
 }  // namespace
 
+tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
+  const bool wide = hash_block == 2 * kHashBlock;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock>
+                          : (const void*)k_owner_hash<kHashBlock>;
+  cudaFuncAttributes fa;
+  TC_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0;
+  TC_CUDA_TRY(cudaGetDevice(&dev));
+  TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t need = owner_hash_smem(chunk) + fa.sharedSizeBytes;
+  return need <= (size_t)optin ? TC_OK : TC_ERR_INVALID_ARG;
+}
+
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   const uint32_t n = g->n;
   const int sms = num_sms();
@@ -761,8 +780,7 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
     g->item_cap = want;
   }
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
-  // two cuckoo tables of chunk + chunk / 4 + 1 slots
-  const size_t smem = sizeof(uint32_t) * 2 * ((size_t)chunk + chunk / 4 + 1);
+  const size_t smem = owner_hash_smem(chunk);
   const bool wide = g->params.hash_block == 2 * kHashBlock;
   const int threads = wide ? 2 * kHashBlock : kHashBlock;
   const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock>

@@ -125,13 +125,14 @@ tc_status tc_params_default(tc_params* p) {
 tc_status tc_set_params(tc_graph* g, const tc_params* p) {
   if (!g || !p) return TC_ERR_INVALID_ARG;
   const uint32_t c = p->hash_chunk;
-  if (c < 32 || c > 16384 || (c & (c - 1)) != 0) return TC_ERR_INVALID_ARG;
+  if (c < 32 || c > 16384 || c % 32 != 0) return TC_ERR_INVALID_ARG;
   if (p->hash_block != 512 && p->hash_block != 1024) return TC_ERR_INVALID_ARG;
   if (p->edges_per_item == 0 || p->edges_per_item > p->hash_block || p->bfs_alpha == 0 ||
       p->bfs_beta == 0)
     return TC_ERR_INVALID_ARG;
   if (p->barrier_timeout_ms == 0 || p->barrier_timeout_ms > 600000) return TC_ERR_INVALID_ARG;
   if (p->medium_max_degree > 1024) return TC_ERR_INVALID_ARG;
+  TC_TRY(owner_hash_fits(c, p->hash_block));
   g->params = *p;
   return TC_OK;
 }

@@ -172,6 +172,9 @@ __device__ __forceinline__ uint32_t batch_graph_of(const unsigned long long* off
   return lo;
 }
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
+// TC_OK if owner-hash blocks of `hash_block` threads with chunks of `chunk`
+// entries fit the device's shared memory per block, else TC_ERR_INVALID_ARG.
+tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block);
 
 // ---- device helpers -----------------------------------------------------
 

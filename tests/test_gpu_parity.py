@@ -178,6 +178,9 @@ def test_errors():
     assert g.count(2) == 0  # the handle stays usable
     with pytest.raises(tc.TCError):
         g.set_params(hash_chunk=100)
+    with pytest.raises(tc.TCError):
+        g.set_params(hash_block=768)
+    assert g.count(2) == 0
     g.close()
 
 
