@@ -66,6 +66,8 @@ def _load():
         lib.orc_triples.argtypes = [ctypes.c_uint32, _u8p]
         lib.orc_forward.restype = ctypes.c_uint64
         lib.orc_forward.argtypes = [ctypes.c_uint32, _i64p, _u32p]
+        lib.orc_cetc_split.restype = ctypes.c_uint64
+        lib.orc_cetc_split.argtypes = [ctypes.c_uint32, _i64p, _u32p, _i32p, _u64p]
         _lib = lib
     return _lib
 
@@ -176,6 +178,16 @@ def forward(row_ptr, col) -> int:
     """Algorithm Forward with decreasing-degree relabelling (independent of BFS)."""
     n = row_ptr.size - 1
     return int(_load().orc_forward(n, _p(row_ptr, _i64p), _p(col, _u32p)))
+
+
+def cetc_split(row_ptr, col, level) -> dict:
+    """Algorithm CETC-Seq-S: T0 (forward-hashed on the horizontal subgraph G0),
+    T1 (hashed intersections of G1 rows over the edges of G0), T = T0 + T1."""
+    n = row_ptr.size - 1
+    out = np.zeros(2, dtype=np.uint64)
+    T = _load().orc_cetc_split(n, _p(row_ptr, _i64p), _p(col, _u32p), _p(level, _i32p),
+                               _p(out, _u64p))
+    return dict(T=int(T), T0=int(out[0]), T1=int(out[1]))
 
 
 def max_degree_root(row_ptr) -> int:

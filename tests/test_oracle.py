@@ -353,3 +353,67 @@ def test_generators_deterministic_and_shaped():
     assert e[0].size == 8192 and e[0].max() < 1024 and e[1].max() < 1024
     ms, md = gen.mesh_edges(4, 5, 1.0, 7)
     assert ms.size == 4 * 4 + 3 * 5 + 3 * 4
+
+
+# --------------------------------------------------------------------------
+# Algorithm CETC-Seq-S (split into G0 and G1)
+# --------------------------------------------------------------------------
+
+def _split(g, root):
+    n, s, d = g
+    rp, col = oracle.build_csr(n, s, d)
+    lv = oracle.bfs_levels(rp, col, root) if n else np.zeros(0, np.int32)
+    return oracle.cetc_split(rp, col, lv)
+
+
+@pytest.mark.parametrize("n", range(1, 13))
+def test_split_complete_graph(n):
+    """K_n from vertex 0: the other n - 1 vertices share level 1, so G0 = K_{n-1}
+    holds C(n-1, 3) triangles and the C(n-1, 2) triangles through the root have
+    their apex on level 0."""
+    r = _split(graphs.complete(n), 0)
+    assert r["T0"] == comb(n - 1, 3) and r["T1"] == comb(n - 1, 2) and r["T"] == comb(n, 3)
+
+
+@pytest.mark.parametrize("n", [5, 6, 9, 31])
+def test_split_wheel(n):
+    """W_n from the hub: G0 is the rim cycle (no triangle for n - 1 >= 4)."""
+    r = _split(graphs.wheel(n), 0)
+    assert (r["T0"], r["T1"]) == (0, n - 1)
+
+
+@pytest.mark.parametrize("rows,cols,p,seed", [(5, 5, 0.5, 7), (17, 9, 1.0, 3)])
+def test_split_mesh(rows, cols, p, seed):
+    """Anti-diagonal mesh from the corner: every apex is off its diagonal's level."""
+    s, d = gen.mesh_edges(rows, cols, p, seed)
+    D = int(gen.mesh_diagonals(rows, cols, p, seed).sum())
+    r = _split((rows * cols, s, d), 0)
+    assert (r["T0"], r["T1"]) == (0, 2 * D)
+
+
+@pytest.mark.parametrize("family,seed", [("er", 1), ("er", 5), ("rmat", 3), ("rmat", 6)])
+def test_split_against_cetc_and_forward(family, seed):
+    """T0 + T1 = T (Forward, an independent count); T1 = c1 and 3 T0 = c2 of
+    the CETC-SM split, for several roots (restarts included)."""
+    if family == "er":
+        n = 2000
+        s, d = gen.er_edges(n, 30000, seed)
+    else:
+        n = 1 << 11
+        s, d = gen.rmat_edges(11, 16, seed)
+    rp, col = oracle.build_csr(n, s, d)
+    f = oracle.forward(rp, col)
+    for root in [0, oracle.max_degree_root(rp), n - 1]:
+        lv = oracle.bfs_levels(rp, col, root)
+        sp = oracle.cetc_split(rp, col, lv)
+        c = oracle.cetc(rp, col, lv)
+        assert sp["T"] == f == c["T"]
+        assert sp["T1"] == c["c1"] and 3 * sp["T0"] == c["c2"]
+
+
+def test_split_disconnected():
+    parts = [graphs.complete(6), graphs.wheel(7), graphs.cycle(3), graphs.path(4),
+             graphs.diag_grid(3, 4), graphs.complete(1)]
+    g = graphs.relabel(graphs.disjoint_union(*parts), 9)
+    for root in range(0, g[0], 7):
+        assert _split(g, root)["T"] == comb(6, 3) + 6 + 1 + 0 + 2 * 2 * 3 + 0
