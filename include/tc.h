@@ -92,6 +92,43 @@ tc_status tc_graph_info(const tc_graph* g, uint32_t* n, uint64_t* m, uint32_t* d
 tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count);
 
 /*
+ * Algorithm CETC-Seq-S (Section "CETC Split Triangle Counting").  BFS levels
+ * from `root` as in tc_count; the edges then split into G0, the horizontal
+ * edges, and G1, the edges between levels.  T0 = the triangles of G0 by
+ * Algorithm forward-hashed (Section "Related Work"; the vertices ranked by
+ * their G0 degree), T1 = the sum over horizontal edges {u, v} of
+ * |N_G1(u) ∩ N_G1(v)|.  *count = T0 + T1, the same count as tc_count's;
+ * tc_get_stats gives c1 = T1 and c2 = 3 T0 (Algorithm CETC-SM's split), and
+ * levels and cover edges can be read as after tc_count.  The first call
+ * allocates the handle's oriented adjacency (n + 1 offsets and m ids).
+ * Errors as tc_count, plus TC_ERR_OOM.
+ */
+tc_status tc_count_split(tc_graph* g, uint32_t root, void* stream, uint64_t* count);
+
+/*
+ * Algorithm Forward with hashed intersections (Section "Related Work"), the
+ * vertices ranked by (degree, id) as in the paper's reordering by degree:
+ * every edge is oriented towards its endpoint of higher rank, A+(x) holds the
+ * ends of x's outgoing edges, and each oriented edge (x, w) adds
+ * |A+(x) ∩ A+(w)|.  No BFS: tc_get_levels and tc_get_cover_edges refuse
+ * (TC_ERR_INVALID_ARG) until the next tc_count.  Allocates as tc_count_split.
+ * Errors: TC_ERR_INVALID_ARG (count == NULL), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+tc_status tc_count_forward(tc_graph* g, void* stream, uint64_t* count);
+
+/*
+ * Algorithm CETC-Seq-FE (Section "CETC Forward Exchanging Triangle Counting"):
+ * BFS from `root`, then the covering ratio c = |S| / m; when c < threshold the
+ * count goes on as tc_count (Algorithm CETC-Seq), otherwise as
+ * tc_count_forward.  The paper's experiments use threshold 0.7.
+ * *used_forward (may be NULL) receives 1 when the forward count ran.  After a
+ * forward count the levels and cover edges are not available.  Errors as
+ * tc_count, plus TC_ERR_INVALID_ARG for a negative or NaN threshold.
+ */
+tc_status tc_count_fe(tc_graph* g, uint32_t root, float threshold, void* stream, uint64_t* count,
+                      int* used_forward);
+
+/*
  * Count k graphs (roots[i] for gs[i]) together (the batched form of the
  * data-parallel Algorithm CETC-SM): the graphs are concatenated into one CSR
  * with per-graph vertex and entry offsets, and every phase runs as one sequence

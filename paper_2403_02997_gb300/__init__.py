@@ -73,6 +73,9 @@ def load_library(path: str = LIB_PATH):
         "tc_graph_info": ([vp, P(u32), P(u64), P(u32)], ctypes.c_int),
         "tc_count": ([vp, u32, vp, P(u64)], ctypes.c_int),
         "tc_count_many": ([P(vp), P(u32), ctypes.c_size_t, vp, P(u64)], ctypes.c_int),
+        "tc_count_split": ([vp, u32, vp, P(u64)], ctypes.c_int),
+        "tc_count_forward": ([vp, vp, P(u64)], ctypes.c_int),
+        "tc_count_fe": ([vp, u32, ctypes.c_float, vp, P(u64), P(ctypes.c_int)], ctypes.c_int),
         "tc_get_levels": ([vp, vp], ctypes.c_int),
         "tc_get_cover_edges": ([vp, P(u64), vp, vp], ctypes.c_int),
         "tc_get_csr": ([vp, vp, vp], ctypes.c_int),
@@ -159,6 +162,28 @@ def tc_count(handle: int, root: int, stream=None) -> int:
     _check(load_library().tc_count(handle, root, _stream_handle(stream), ctypes.byref(c)),
            "tc_count")
     return int(c.value)
+
+
+def tc_count_split(handle, root: int, stream=None) -> int:
+    c = ctypes.c_uint64()
+    _check(load_library().tc_count_split(handle, root, _stream_handle(stream), ctypes.byref(c)),
+           "tc_count_split")
+    return int(c.value)
+
+
+def tc_count_forward(handle, stream=None) -> int:
+    c = ctypes.c_uint64()
+    _check(load_library().tc_count_forward(handle, _stream_handle(stream), ctypes.byref(c)),
+           "tc_count_forward")
+    return int(c.value)
+
+
+def tc_count_fe(handle, root: int, threshold: float, stream=None):
+    c = ctypes.c_uint64()
+    used = ctypes.c_int()
+    _check(load_library().tc_count_fe(handle, root, threshold, _stream_handle(stream),
+                                      ctypes.byref(c), ctypes.byref(used)), "tc_count_fe")
+    return int(c.value), bool(used.value)
 
 
 def tc_count_many(handles: Sequence[int], roots: Sequence[int], stream=None) -> list:
@@ -259,6 +284,18 @@ class Graph:
         if root is None:
             root = 0
         return tc_count(self.handle, root, stream)
+
+    def count_split(self, root: Optional[int] = None, stream=None) -> int:
+        """Algorithm CETC-Seq-S (see tc_count_split)."""
+        return tc_count_split(self.handle, 0 if root is None else root, stream)
+
+    def count_forward(self, stream=None) -> int:
+        """Algorithm Forward with degree ranking (see tc_count_forward)."""
+        return tc_count_forward(self.handle, stream)
+
+    def count_fe(self, root: Optional[int] = None, threshold: float = 0.7, stream=None):
+        """Algorithm CETC-Seq-FE: (count, whether the forward count ran)."""
+        return tc_count_fe(self.handle, 0 if root is None else root, threshold, stream)
 
     def max_degree_vertex(self) -> int:
         return tc_max_degree_vertex(self.handle)

@@ -428,6 +428,16 @@ __global__ void k_item_owner(const unsigned long long* __restrict__ ioff, uint32
 
 // ---- the owner-hash kernel ----------------------------------------------
 
+// Row ranges of an owner-hash pass (see k_owner_hash).
+struct HashRows {
+  const unsigned long long* tb;  // owner h's table: tcol[tb[h], te[h])
+  const unsigned long long* te;
+  const uint32_t* tcol;
+  const unsigned long long* sb;  // streamer x's (first) segment: scol[sb[x], se[x])
+  const unsigned long long* se;
+  const uint32_t* scol;
+};
+
 // Shared memory of k_owner_hash: the chunk's hash tables (or its sorted copy).
 extern __shared__ uint32_t s_table[];
 
@@ -601,15 +611,28 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // chunk's largest id (rows are sorted: cursors only move forward, and each
 // streamed element is looked up in exactly one chunk; the last chunk takes the
 // rest).  Warps take edges one at a time from a shared counter.
-template <int kThreads>
+//
+// The rows are given as HashRows.  Cover edges of Algorithm CETC-Seq
+// (kPlain = false): the owner's table is its whole row, col[tb[h], te[h]) with
+// tb = row_ptr, te = row_ptr + 1, and the streamer x streams two segments of
+// its level-split row scol = lcol: [sb[x], se[x]) (sb = row_ptr, se = lsplit:
+// the other-level part, tallied as c1) and its same-level part above v,
+// [first id > v in [se[x], te[x]), te[x]) (tallied as c2').  Plain pairs
+// (kPlain = true): the table is tcol[tb[h], te[h]) and the streamer streams the
+// one segment scol[sb[x], se[x]); hits are tallied as c1, or as c2' when
+// plain_as_c2 is set.
+template <int kThreads, bool kPlain>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
-    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-    const uint32_t* __restrict__ lcol, const unsigned long long* __restrict__ lsplit,
-    const unsigned long long* __restrict__ ooff, const uint32_t* __restrict__ ostream,
-    const unsigned long long* __restrict__ ioff, const uint32_t* __restrict__ item_owner,
-    unsigned long long nitems, uint32_t chunk, uint32_t per_item, uint32_t force_sorted,
+    const HashRows rows, const unsigned long long* __restrict__ ooff,
+    const uint32_t* __restrict__ ostream, const unsigned long long* __restrict__ ioff,
+    const uint32_t* __restrict__ item_owner, unsigned long long nitems, uint32_t chunk,
+    uint32_t per_item, uint32_t force_sorted, uint32_t plain_as_c2,
     const unsigned long long* __restrict__ voff, uint32_t nb,
     unsigned long long* __restrict__ gcount, DevCounters* ctr) {
+  const unsigned long long* __restrict__ tb = rows.tb;
+  const unsigned long long* __restrict__ te = rows.te;
+  const uint32_t* __restrict__ col = rows.tcol;
+  const uint32_t* __restrict__ lcol = rows.scol;
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
   // cursors of the slice's edges (edges_per_item <= kThreads)
@@ -623,19 +646,24 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const unsigned long long item = s_item;
     if (item >= nitems) break;
     const uint32_t h = item_owner[item];
-    const unsigned long long hb = row_ptr[h], he = row_ptr[h + 1];
+    const unsigned long long hb = tb[h], he = te[h];
     const uint32_t chunks = (uint32_t)((he - hb + chunk - 1) / chunk);
     const unsigned long long eb = ooff[h] + (item - ioff[h]) * per_item;
     unsigned long long item_hits = 0;  // this thread's hits in this item (batch mode)
     const uint32_t ne = (uint32_t)min((unsigned long long)per_item, ooff[h + 1] - eb);
     for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x) {
       const uint32_t x = ostream[eb + i];
-      const uint32_t v = x > h ? x : h;
-      const unsigned long long sp = lsplit[x], xe = row_ptr[x + 1];
-      s_a[i] = row_ptr[x];
+      const unsigned long long sp = rows.se[x];
+      s_a[i] = rows.sb[x];
       s_ae[i] = sp;
-      s_b[i] = lower_bound_u32(lcol, sp, xe, v + 1);
-      s_be[i] = xe;
+      if (kPlain) {
+        s_b[i] = s_be[i] = 0;
+      } else {
+        const uint32_t v = x > h ? x : h;
+        const unsigned long long xe = te[x];
+        s_b[i] = lower_bound_u32(lcol, sp, xe, v + 1);
+        s_be[i] = xe;
+      }
     }
     for (uint32_t c = 0; c < chunks; ++c) {
       const unsigned long long cb = hb + (unsigned long long)c * chunk;
@@ -680,8 +708,12 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
           s_b[i] = r.b;
         }
         const uint32_t c1 = r.c1, c2c = r.c2c;
-        tl.c1 += c1;
-        tl.c2c += c2c;
+        if (kPlain && plain_as_c2) {
+          tl.c2c += c1;
+        } else {
+          tl.c1 += c1;
+          tl.c2c += c2c;
+        }
         item_hits += c1 + c2c;
       }
       __syncthreads();
@@ -696,48 +728,209 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
 
 }  // namespace
 
-tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
-  const bool wide = hash_block == 2 * kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock>
-                          : (const void*)k_owner_hash<kHashBlock>;
-  cudaFuncAttributes fa;
-  TC_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-  int dev = 0, optin = 0;
-  TC_CUDA_TRY(cudaGetDevice(&dev));
-  TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t need = owner_hash_smem(chunk) + fa.sharedSizeBytes;
-  return need <= (size_t)optin ? TC_OK : TC_ERR_INVALID_ARG;
+namespace {
+
+// ---- Algorithm Forward and Algorithm CETC-Seq-S --------------------------
+
+// deg[x] = end[x] - beg[x]: the lengths of the rows an orientation ranks by.
+__global__ void k_row_degrees(const unsigned long long* __restrict__ beg,
+                              const unsigned long long* __restrict__ end, uint32_t n,
+                              uint32_t* __restrict__ deg) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x)
+    deg[x] = (uint32_t)(end[x] - beg[x]);
 }
 
-tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
+// The orientation of Algorithm Forward (Section "Related Work"), ranking the
+// vertices by degree as the paper's reordering does: A+(x) = the w in
+// arr[beg[x], end[x]) with (deg[w], w) > (deg[x], x), kept in ascending id
+// order.  Every edge of the row set lies in exactly one A+(), and
+// |A+(x)| <= sqrt(2 m).  One warp per row; with out == nullptr it writes
+// |A+(x)| to cnt[x], else A+(x) to out[obeg[x] ...] (ballot ranks keep order).
+__global__ void k_orient(const unsigned long long* __restrict__ beg,
+                         const unsigned long long* __restrict__ end,
+                         const uint32_t* __restrict__ arr, const uint32_t* __restrict__ deg,
+                         uint32_t n, uint32_t* __restrict__ cnt,
+                         const unsigned long long* __restrict__ obeg,
+                         uint32_t* __restrict__ out) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t warps = (uint64_t)gridDim.x * blockDim.x / 32;
+  for (uint64_t xx = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; xx < n; xx += warps) {
+    const uint32_t x = (uint32_t)xx;
+    const unsigned long long b = beg[x], e = end[x];
+    const uint32_t dx = deg[x];
+    unsigned long long pos = out ? obeg[x] : 0;
+    uint32_t c = 0;
+    for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+      const unsigned long long j = j0 + lane;
+      bool keep = false;
+      uint32_t w = 0;
+      if (j < e) {
+        w = arr[j];
+        const uint32_t dw = deg[w];
+        keep = dw > dx || (dw == dx && w > x);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (out && keep) out[pos + __popc(m & lt)] = w;
+      pos += __popc(m);
+      c += __popc(m);
+    }
+    if (!out && lane == 0) cnt[x] = c;
+  }
+}
+
+// Pairs of an oriented adjacency (obeg, ocol), one thread per entry (x, w):
+// |A+(x) ∩ A+(w)| counts each triangle of the row set once (at its two
+// lowest-ranked vertices).  Both lists of at most small_max ids: merged by the
+// thread (two pointers); otherwise the pair goes to the owner-hash pass as
+// (owner, streamer), the owner holding the longer list (ties: larger id).
+// Hits are tallied as c1, or as c2' when as_c2 is set.
+__global__ void __launch_bounds__(kCoverBlock) k_forward_pairs(
+    const unsigned long long* __restrict__ obeg, const uint32_t* __restrict__ ocol, uint32_t n,
+    unsigned long long total, uint32_t small_max, uint32_t as_c2, uint2* __restrict__ large,
+    uint32_t* __restrict__ ocount, DevCounters* ctr) {
+  __shared__ uint32_t s_lo, s_hi;
+  Tally tl;
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < total;
+       e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
+    const unsigned long long e1 = min(total, e0 + kCoverEntriesPerBlock);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_lo = row_of(obeg, 0, n - 1, e0);
+      s_hi = row_of(obeg, s_lo, n - 1, e1 - 1);
+    }
+    __syncthreads();
+    const uint32_t lo = s_lo, hi = s_hi;
+    for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
+      const unsigned long long j = b + threadIdx.x;
+      bool is_large = false;
+      uint2 le = make_uint2(0, 0);
+      if (j < e1) {
+        const uint32_t x = row_of(obeg, lo, hi, j);
+        const uint32_t w = ocol[j];
+        const unsigned long long bx = obeg[x], ex = obeg[x + 1];
+        const unsigned long long bw = obeg[w], ew = obeg[w + 1];
+        const unsigned long long dx = ex - bx, dw = ew - bw;
+        if (dw > 0) {
+          if (dx <= small_max && dw <= small_max) {
+            unsigned long long p = bx, q = bw;
+            uint32_t here = 0;
+            while (p < ex && q < ew) {
+              const uint32_t a = ocol[p], c = ocol[q];
+              here += a == c;
+              p += a <= c;
+              q += c <= a;
+            }
+            if (as_c2) tl.c2c += here; else tl.c1 += here;
+          } else {
+            is_large = true;
+            const bool w_owns = dw > dx || (dw == dx && w > x);
+            le = w_owns ? make_uint2(w, x) : make_uint2(x, w);
+            atomicAdd(&ocount[le.x], 1u);
+          }
+        }
+      }
+      warp_append_pair(is_large, le, large, &ctr->num_large);
+    }
+  }
+  flush_tally(tl, ctr);
+}
+
+// The cover edges of Algorithm CETC-Seq-S: one thread per adjacency entry
+// (u, v); a horizontal edge with u < v joins the cover list, and the
+// intersection of its endpoints' G1 rows (the other-level parts of the
+// level-split rows, lcol[row_ptr[x], lsplit[x])) is merged by the thread when
+// both have at most small_max ids, else sent to the owner-hash pass (owner:
+// the longer G1 row, ties larger id).  Hits are tallied as c1.
+__global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, const uint32_t* __restrict__ lcol,
+    const unsigned long long* __restrict__ lsplit, uint32_t n, unsigned long long nnz,
+    uint32_t small_max, uint2* __restrict__ cover, uint2* __restrict__ large,
+    uint32_t* __restrict__ ocount, DevCounters* ctr) {
+  __shared__ uint32_t s_lo, s_hi;
+  Tally tl;
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
+       e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
+    const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_lo = row_of(row_ptr, 0, n - 1, e0);
+      s_hi = row_of(row_ptr, s_lo, n - 1, e1 - 1);
+    }
+    __syncthreads();
+    const uint32_t lo = s_lo, hi = s_hi;
+    for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
+      const unsigned long long j = b + threadIdx.x;
+      bool is_cover = false, is_large = false;
+      uint2 ce = make_uint2(0, 0), le = make_uint2(0, 0);
+      if (j < e1) {
+        const uint32_t u = row_of(row_ptr, lo, hi, j);
+        const uint32_t v = col[j];
+        if (v > u && level[v] == level[u]) {
+          is_cover = true;
+          ce = make_uint2(u, v);
+          const unsigned long long bu = row_ptr[u], eu = lsplit[u];
+          const unsigned long long bv = row_ptr[v], ev = lsplit[v];
+          const unsigned long long du = eu - bu, dv = ev - bv;
+          if (du > 0 && dv > 0) {
+            if (du <= small_max && dv <= small_max) {
+              unsigned long long p = bu, q = bv;
+              uint32_t here = 0;
+              while (p < eu && q < ev) {
+                const uint32_t a = lcol[p], c = lcol[q];
+                here += a == c;
+                p += a <= c;
+                q += c <= a;
+              }
+              tl.c1 += here;
+            } else {
+              is_large = true;
+              const bool v_owns = dv > du || (dv == du && v > u);
+              le = v_owns ? make_uint2(v, u) : make_uint2(u, v);
+              atomicAdd(&ocount[le.x], 1u);
+            }
+          }
+        }
+      }
+      warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
+      warp_append_pair(is_large, le, large, &ctr->num_large);
+    }
+  }
+  flush_tally(tl, ctr);
+}
+
+// |S|: the horizontal edges {u, v}, u < v (one thread per adjacency entry).
+__global__ void __launch_bounds__(kCoverBlock) k_horizontal(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, uint32_t n, unsigned long long nnz, DevCounters* ctr) {
+  __shared__ uint32_t s_lo, s_hi;
+  unsigned long long mine = 0;
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
+       e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
+    const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_lo = row_of(row_ptr, 0, n - 1, e0);
+      s_hi = row_of(row_ptr, s_lo, n - 1, e1 - 1);
+    }
+    __syncthreads();
+    const uint32_t lo = s_lo, hi = s_hi;
+    for (unsigned long long j = e0 + threadIdx.x; j < e1; j += kCoverBlock) {
+      const uint32_t u = row_of(row_ptr, lo, hi, j);
+      const uint32_t v = col[j];
+      mine += v > u && level[v] == level[u];
+    }
+  }
+  mine = warp_sum(mine);
+  if (lane_id() == 0 && mine) atomicAdd(&ctr->num_cover, mine);
+}
+
+// Level-split rows of the whole graph: short rows by warps, long rows in tiles.
+tc_status run_level_split(tc_graph* g, cudaStream_t st) {
   const uint32_t n = g->n;
   const int sms = num_sms();
-  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
-  if (g->nnz == 0) {
-    TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
-    return TC_OK;
-  }
-  TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
-  const uint32_t small_max = g->params.small_max_degree;
-  k_cover<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
-      g->params.medium_max_degree > kMediumCap ? kMediumCap : g->params.medium_max_degree,
-      g->medium, g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
-  TC_CUDA_TRY(cudaGetLastError());
-  TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
-  TC_TRY(exclusive_scan_u32(g->ocount, g->ooff, n, g->scan, st));
-  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-  TC_CUDA_TRY(cudaStreamSynchronize(st));
-  const unsigned long long nmedium = g->ctr_host->num_medium;
-  if (nmedium > 0) {
-    k_warp_merge<<<grid_for(nmedium * 32, kWarpMergeBlock, sms * 16), kWarpMergeBlock, 0, st>>>(
-        g->row_ptr, g->col, g->level, g->medium, nmedium, g->voff, g->batch_k, g->gcount,
-        g->ctr); TC_LAUNCHED();
-    TC_CUDA_TRY(cudaGetLastError());
-  }
-  const unsigned long long nlarge = g->ctr_host->num_large;
-  if (nlarge == 0) return TC_OK;
-  // level-split rows: short rows by warps, long rows in tiles
   k_level_split<<<sms * 16, 256, 0, st>>>(g->row_ptr, g->col, g->level, n, g->lcol, g->lsplit); TC_LAUNCHED();
   if (g->d_max > kSplitMax) {
     k_split_tiles<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->row_ptr, n, g->fdeg); TC_LAUNCHED();
@@ -756,6 +949,20 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
                                                                  g->lcol, g->lsplit); TC_LAUNCHED();
     }
   }
+  TC_CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+// One owner-hash pass over the nlarge (owner, streamer) pairs in g->large,
+// whose per-owner counts are in g->ocount and their exclusive scan in g->ooff:
+// bucket the streamers by owner, slice each owner's bucket into work items of
+// edges_per_item, and launch k_owner_hash over the items.
+template <bool kPlain>
+tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows& rows,
+                         uint32_t plain_as_c2, const unsigned long long* voff, uint32_t nb,
+                         unsigned long long* gcount, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
   TC_CUDA_TRY(cudaMemsetAsync(g->ofill, 0, sizeof(uint32_t) * n, st));
   k_bucket<<<grid_for(nlarge, 256, sms * 16), 256, 0, st>>>(g->large, nlarge, g->ooff, g->ofill,
                                                            g->ostream); TC_LAUNCHED();
@@ -783,8 +990,8 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   const size_t smem = owner_hash_smem(chunk);
   const bool wide = g->params.hash_block == 2 * kHashBlock;
   const int threads = wide ? 2 * kHashBlock : kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock>
-                          : (const void*)k_owner_hash<kHashBlock>;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, kPlain>
+                          : (const void*)k_owner_hash<kHashBlock, kPlain>;
   TC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -794,15 +1001,174 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
   const uint32_t force_sorted = g->params.sorted_lookup ? 1u : 0u;
   if (wide)
-    k_owner_hash<2 * kHashBlock><<<grid, threads, smem, st>>>(
-        g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff, g->ostream, g->ioff, g->item_owner,
-        nitems, chunk, per_item, force_sorted, g->voff, g->batch_k, g->gcount, g->ctr);
+    k_owner_hash<2 * kHashBlock, kPlain><<<grid, threads, smem, st>>>(
+        rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
+        plain_as_c2, voff, nb, gcount, g->ctr);
   else
-    k_owner_hash<kHashBlock><<<grid, threads, smem, st>>>(
-        g->row_ptr, g->col, g->lcol, g->lsplit, g->ooff, g->ostream, g->ioff, g->item_owner,
-        nitems, chunk, per_item, force_sorted, g->voff, g->batch_k, g->gcount, g->ctr);
+    k_owner_hash<kHashBlock, kPlain><<<grid, threads, smem, st>>>(
+        rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
+        plain_as_c2, voff, nb, gcount, g->ctr);
   TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+// Scan of the per-owner counts and the number of owner-path pairs.
+tc_status scan_owners(tc_graph* g, cudaStream_t st, unsigned long long* nlarge) {
+  TC_TRY(exclusive_scan_u32(g->ocount, g->ooff, g->n, g->scan, st));
+  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  *nlarge = g->ctr_host->num_large;
+  return TC_OK;
+}
+
+}  // namespace
+
+tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
+  const bool wide = hash_block == 2 * kHashBlock;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, false>
+                          : (const void*)k_owner_hash<kHashBlock, false>;
+  cudaFuncAttributes fa;
+  TC_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0;
+  TC_CUDA_TRY(cudaGetDevice(&dev));
+  TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t need = owner_hash_smem(chunk) + fa.sharedSizeBytes;
+  return need <= (size_t)optin ? TC_OK : TC_ERR_INVALID_ARG;
+}
+
+tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  if (g->nnz == 0) {
+    TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+    return TC_OK;
+  }
+  TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
+  const uint32_t small_max = g->params.small_max_degree;
+  k_cover<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
+      g->params.medium_max_degree > kMediumCap ? kMediumCap : g->params.medium_max_degree,
+      g->medium, g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+  unsigned long long nlarge = 0;
+  TC_TRY(scan_owners(g, st, &nlarge));
+  const unsigned long long nmedium = g->ctr_host->num_medium;
+  if (nmedium > 0) {
+    k_warp_merge<<<grid_for(nmedium * 32, kWarpMergeBlock, sms * 16), kWarpMergeBlock, 0, st>>>(
+        g->row_ptr, g->col, g->level, g->medium, nmedium, g->voff, g->batch_k, g->gcount,
+        g->ctr); TC_LAUNCHED();
+    TC_CUDA_TRY(cudaGetLastError());
+  }
+  if (nlarge == 0) return TC_OK;
+  TC_TRY(run_level_split(g, st));
+  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->row_ptr, g->lsplit, g->lcol};
+  return run_owner_pass<false>(g, nlarge, rows, 0, g->voff, g->batch_k, g->gcount, st);
+}
+
+namespace {
+
+// Oriented adjacency storage (obeg[n+1], ocol[m]), allocated on first use.
+tc_status ensure_oriented(tc_graph* g) {
+  if (!g->obeg) TC_CUDA_TRY(cudaMalloc(&g->obeg, sizeof(unsigned long long) * ((size_t)g->n + 1)));
+  if (!g->ocol) TC_CUDA_TRY(cudaMalloc(&g->ocol, sizeof(uint32_t) * ((size_t)g->m + 1)));
+  return TC_OK;
+}
+
+// A+() of the rows arr[beg[x], end[x]) into (g->obeg, g->ocol); *total = its size.
+tc_status orient(tc_graph* g, const unsigned long long* beg, const unsigned long long* end,
+                 const uint32_t* arr, cudaStream_t st, unsigned long long* total) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  TC_TRY(ensure_oriented(g));
+  k_row_degrees<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(beg, end, n, g->fdeg); TC_LAUNCHED();
+  k_orient<<<sms * 16, 256, 0, st>>>(beg, end, arr, g->fdeg, n, g->ocount, nullptr, nullptr); TC_LAUNCHED();
+  TC_TRY(exclusive_scan_u32(g->ocount, g->obeg, n, g->scan, st));
+  TC_CUDA_TRY(cudaMemcpyAsync(&g->ctr_host->scan_total, g->obeg + n, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  *total = g->ctr_host->scan_total;
+  if (*total > g->m) return TC_ERR_OVERFLOW;  // every edge lies in one A+() at most
+  k_orient<<<sms * 16, 256, 0, st>>>(beg, end, arr, g->fdeg, n, nullptr, g->obeg, g->ocol); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+// The pairs of the oriented adjacency in (g->obeg, g->ocol): inline merges and
+// one owner-hash pass.
+tc_status forward_pairs(tc_graph* g, unsigned long long total, uint32_t as_c2, cudaStream_t st) {
+  if (total == 0) return TC_OK;
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
+  TC_CUDA_TRY(cudaMemsetAsync(&g->ctr->num_large, 0, sizeof(unsigned long long), st));
+  k_forward_pairs<<<grid_for(total, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+      g->obeg, g->ocol, n, total, g->params.small_max_degree, as_c2, g->large, g->ocount, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  unsigned long long nlarge = 0;
+  TC_TRY(scan_owners(g, st, &nlarge));
+  if (nlarge == 0) return TC_OK;
+  const HashRows rows{g->obeg, g->obeg + 1, g->ocol, g->obeg, g->obeg + 1, g->ocol};
+  return run_owner_pass<true>(g, nlarge, rows, as_c2, nullptr, 0, nullptr, st);
+}
+
+}  // namespace
+
+tc_status run_forward_count(tc_graph* g, cudaStream_t st) {
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  if (g->nnz == 0) {
+    TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+    return TC_OK;
+  }
+  unsigned long long total = 0;
+  TC_TRY(orient(g, g->row_ptr, g->row_ptr + 1, g->col, st, &total));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+  return forward_pairs(g, total, 0, st);
+}
+
+tc_status run_split_count(tc_graph* g, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  if (g->nnz == 0) {
+    TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+    return TC_OK;
+  }
+  // G1 rows are the other-level parts, G0 rows the same-level parts, of the
+  // level-split rows
+  TC_TRY(run_level_split(g, st));
+  // T1: intersections of G1 rows over the edges of G0 (the cover edges)
+  TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
+  k_g1_pairs<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+      g->row_ptr, g->col, g->level, g->lcol, g->lsplit, n, g->nnz, g->params.small_max_degree,
+      g->cover, g->large, g->ocount, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+  unsigned long long nlarge = 0;
+  TC_TRY(scan_owners(g, st, &nlarge));
+  if (nlarge > 0) {
+    const HashRows rows{g->row_ptr, g->lsplit, g->lcol, g->row_ptr, g->lsplit, g->lcol};
+    TC_TRY(run_owner_pass<true>(g, nlarge, rows, 0, nullptr, 0, nullptr, st));
+  }
+  // T0: Algorithm forward-hashed on G0, tallied as c2' (c2 = 3 T0)
+  unsigned long long total = 0;
+  TC_TRY(orient(g, g->lsplit, g->row_ptr + 1, g->lcol, st, &total));
+  return forward_pairs(g, total, 1, st);
+}
+
+tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long* num_cover) {
+  const int sms = num_sms();
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  if (g->nnz > 0) {
+    k_horizontal<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+        g->row_ptr, g->col, g->level, g->n, g->nnz, g->ctr); TC_LAUNCHED();
+    TC_CUDA_TRY(cudaGetLastError());
+  }
+  TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  *num_cover = g->ctr_host->num_cover;
   return TC_OK;
 }
 

@@ -49,7 +49,8 @@ void free_graph(tc_graph* g) {
   void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
                   g->ooff,    g->ioff,  g->parent, g->fdeg,    g->ocount,  g->ofill,
                   g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums,
-                  g->lcol,    g->lsplit, g->tile_row, g->tile_cnt, g->medium};
+                  g->lcol,    g->lsplit, g->tile_row, g->tile_cnt, g->medium, g->obeg,
+                  g->ocol};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -215,23 +216,11 @@ tc_status tc_max_degree_vertex(const tc_graph* g, uint32_t* v) {
   return TC_OK;
 }
 
-tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
-  if (!g || !count) return TC_ERR_INVALID_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::memset(&g->stats, 0, sizeof(g->stats));
-  g->stats.m = g->m;
-  g->counted = false;
-  if (g->n == 0) {
-    *count = 0;
-    g->counted = true;
-    return TC_OK;
-  }
-  if (root >= g->n) return TC_ERR_INVALID_ARG;
-  const uint32_t launches0 = g_launches;
-  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
-  TC_TRY(run_bfs(g, root, st));
-  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
-  TC_TRY(run_cover_and_count(g, st));
+namespace {
+
+// Reads the counters of a count run on `st` (which events 0..3 bracket) into
+// *count and the handle's statistics.
+tc_status finish_count(tc_graph* g, cudaStream_t st, uint64_t* count, uint32_t launches0) {
   TC_CUDA_TRY(cudaEventRecord(g->ev[3], st));
   TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   TC_TRY(sync_status(g, st));
@@ -253,8 +242,101 @@ tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
   g->stats.launches = g_launches - launches0;
   g->stats.hash_items = c.items;
   g->stats.hash_edges = c.num_large;
+  return TC_OK;
+}
+
+// Common start of a count: statistics reset, argument checks.  Returns false
+// (with *status set) when the count is finished or refused here.
+bool begin_count(tc_graph* g, uint32_t root, bool needs_root, uint64_t* count, tc_status* status) {
+  *status = TC_OK;
+  if (!g || !count) {
+    *status = TC_ERR_INVALID_ARG;
+    return false;
+  }
+  std::memset(&g->stats, 0, sizeof(g->stats));
+  g->stats.m = g->m;
+  g->counted = false;
+  if (g->n == 0) {
+    *count = 0;
+    g->counted = true;
+    return false;
+  }
+  if (needs_root && root >= g->n) {
+    *status = TC_ERR_INVALID_ARG;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
+  tc_status s;
+  if (!begin_count(g, root, true, count, &s)) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_TRY(run_bfs(g, root, st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  TC_TRY(run_cover_and_count(g, st));
+  TC_TRY(finish_count(g, st, count, launches0));
   g->counted = true;
   g->last_root = root;
+  return TC_OK;
+}
+
+tc_status tc_count_split(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
+  tc_status s;
+  if (!begin_count(g, root, true, count, &s)) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_TRY(run_bfs(g, root, st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  TC_TRY(run_split_count(g, st));
+  TC_TRY(finish_count(g, st, count, launches0));
+  g->counted = true;
+  g->last_root = root;
+  return TC_OK;
+}
+
+tc_status tc_count_forward(tc_graph* g, void* stream, uint64_t* count) {
+  tc_status s;
+  if (!begin_count(g, 0, false, count, &s)) return s;
+  g->counted = false;  // no levels or cover set behind this count
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  TC_TRY(run_forward_count(g, st));
+  return finish_count(g, st, count, launches0);
+}
+
+tc_status tc_count_fe(tc_graph* g, uint32_t root, float threshold, void* stream, uint64_t* count,
+                      int* used_forward) {
+  tc_status s;
+  if (used_forward) *used_forward = 0;
+  if (!begin_count(g, root, true, count, &s)) return s;
+  if (!(threshold >= 0.f)) return TC_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_TRY(run_bfs(g, root, st));
+  unsigned long long num_cover = 0;
+  TC_TRY(run_count_horizontal(g, st, &num_cover));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  const double c = g->m ? (double)num_cover / (double)g->m : 0.0;
+  if (c < threshold) {
+    TC_TRY(run_cover_and_count(g, st));
+    TC_TRY(finish_count(g, st, count, launches0));
+    g->counted = true;
+    g->last_root = root;
+    return TC_OK;
+  }
+  if (used_forward) *used_forward = 1;
+  TC_TRY(run_forward_count(g, st));
+  TC_TRY(finish_count(g, st, count, launches0));
+  g->stats.num_cover = num_cover;
   return TC_OK;
 }
 

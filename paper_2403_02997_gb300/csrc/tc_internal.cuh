@@ -80,6 +80,8 @@ struct tc_graph {
   uint32_t* ostream = nullptr;   // [m]  streamers bucketed by owner
   uint32_t* lcol = nullptr;      // [nnz] rows reordered [other-level | same-level] per count
   unsigned long long* lsplit = nullptr;  // [n] start of the same-level part of each row
+  unsigned long long* obeg = nullptr;  // [n+1] oriented adjacency A+() (forward counts), on first use
+  uint32_t* ocol = nullptr;            // [m]
   uint32_t* tile_row = nullptr;  // [tile_cap] row of each tile of a long row (level split)
   uint32_t* tile_cnt = nullptr;  // [tile_cap] other-level entries per tile
   unsigned long long tile_cap = 0;
@@ -175,6 +177,12 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
 // TC_OK if owner-hash blocks of `hash_block` threads with chunks of `chunk`
 // entries fit the device's shared memory per block, else TC_ERR_INVALID_ARG.
 tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block);
+// Algorithm Forward (degree orientation) over the whole graph; counters in g->ctr.
+tc_status run_forward_count(tc_graph* g, cudaStream_t st);
+// Algorithm CETC-Seq-S after run_bfs: c1 = T1, c2 = 3 T0, tri = T0 + T1.
+tc_status run_split_count(tc_graph* g, cudaStream_t st);
+// |S| after run_bfs (resets g->ctr).
+tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long* num_cover);
 
 // ---- device helpers -----------------------------------------------------
 

@@ -27,6 +27,7 @@ def declared_functions():
 def test_header_declares_the_abi():
     names = declared_functions()
     for want in ["tc_graph_create", "tc_graph_destroy", "tc_count", "tc_count_many",
+                 "tc_count_split", "tc_count_forward", "tc_count_fe",
                  "tc_get_levels", "tc_get_cover_edges", "tc_status_string"]:
         assert want in names
 
@@ -49,6 +50,9 @@ def test_host_side_argument_checks(lib):
     assert lib.tc_graph_create(None, None, 5, 4, 0, None, ctypes.byref(out)) == 1
     assert lib.tc_graph_create(None, None, 0, 1 << 31, 0, None, ctypes.byref(out)) == 1
     assert lib.tc_count(None, 0, None, None) == 1
+    assert lib.tc_count_split(None, 0, None, None) == 1
+    assert lib.tc_count_forward(None, None, None) == 1
+    assert lib.tc_count_fe(None, 0, 0.7, None, None, None) == 1
     assert lib.tc_count_many(None, None, 0, None, None) == 0
     assert lib.tc_graph_destroy(None) == 0
     p = tc.tc_params()
