@@ -425,6 +425,21 @@ def run_ours(args, world, rank, local):
     survey_bytes = int(24 * m + 12 * spec.n + 16 * n_cover +
                        4 * (deg[cu].sum() + deg[cv].sum()) + 4 * (st["c1"] + st["c2"]))
     del rp, col, cu, cv, deg
+
+    # the paper's variants on the same graph and root (same count; not the headline)
+    variants = {}
+    for name, fn in (("cetc_seq_s", lambda: g.count_split(root, stream=stream)),
+                     ("forward_degree_ranked", lambda: g.count_forward(stream=stream))):
+        fn()
+        ms = []
+        for _ in range(3):
+            assert fn() == T, name
+            ms.append(g.stats()["ms_total"])
+        variants[name] = {"ms": statistics.median(ms), "edges_per_s": m / (statistics.median(ms) / 1e3)}
+    fe_count, fe_forward = g.count_fe(root, 0.7, stream=stream)
+    assert fe_count == T
+    variants["cetc_seq_fe_0.7"] = {"covering_ratio": n_cover / max(m, 1),
+                                   "ran": "forward" if fe_forward else "cetc_seq"}
     peak, peak_kind = measured_peaks()
     hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
     achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0
@@ -489,6 +504,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     g.close()
