@@ -70,6 +70,21 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
                           uint32_t num_vertices, int edges_on_device, void* stream,
                           tc_graph** out);
 
+/*
+ * Degree ordering, the pre-processing of Algorithms CETC-Seq-D and CETC-Seq-SD
+ * (Section "Experimental Results"; the reordering "in decreasing order of their
+ * degrees" of Section "Related Work"): a new graph whose vertex i is the old
+ * vertex host_old_of_new[i], the vertices taken by decreasing degree, ties by
+ * increasing id (so the new vertex 0 has the largest degree).  tc_count on the
+ * new handle is Algorithm CETC-Seq-D and tc_count_split is CETC-Seq-SD; the
+ * count equals the original graph's, while levels and cover edges are those of
+ * the relabelled graph.  host_old_of_new (n entries) may be NULL.  The new
+ * handle copies g's tunables and is independent of g (destroy both).  Errors:
+ * TC_ERR_INVALID_ARG (g or out NULL), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+tc_status tc_graph_relabel_degree(const tc_graph* g, void* stream, tc_graph** out,
+                                  uint32_t* host_old_of_new);
+
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 tc_status tc_graph_destroy(tc_graph* g);
 

@@ -190,6 +190,22 @@ def cetc_split(row_ptr, col, level) -> dict:
     return dict(T=int(T), T0=int(out[0]), T1=int(out[1]))
 
 
+def degree_order(row_ptr) -> np.ndarray:
+    """Degree ordering (the pre-processing of Algorithms CETC-Seq-D / -SD): the
+    old ids by decreasing degree, ties by increasing id; entry i is the old id
+    of new vertex i."""
+    n = row_ptr.size - 1
+    deg = np.diff(np.asarray(row_ptr, dtype=np.int64))
+    return np.lexsort((np.arange(n), -deg)).astype(np.uint32)
+
+
+def relabel_edges(old_of_new, src, dst):
+    """The edge list with every id replaced by its new id."""
+    new_of_old = np.empty_like(old_of_new)
+    new_of_old[old_of_new] = np.arange(old_of_new.size, dtype=old_of_new.dtype)
+    return new_of_old[np.asarray(src, np.int64)], new_of_old[np.asarray(dst, np.int64)]
+
+
 def max_degree_root(row_ptr) -> int:
     """Smallest id among the vertices of maximum degree (0 for an empty graph)."""
     if row_ptr.size <= 1:

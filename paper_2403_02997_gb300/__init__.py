@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
         "tc_count": ([vp, u32, vp, P(u64)], ctypes.c_int),
         "tc_count_many": ([P(vp), P(u32), ctypes.c_size_t, vp, P(u64)], ctypes.c_int),
         "tc_count_split": ([vp, u32, vp, P(u64)], ctypes.c_int),
+        "tc_graph_relabel_degree": ([vp, vp, P(vp), vp], ctypes.c_int),
         "tc_count_forward": ([vp, vp, P(u64)], ctypes.c_int),
         "tc_count_fe": ([vp, u32, ctypes.c_float, vp, P(u64), P(ctypes.c_int)], ctypes.c_int),
         "tc_get_levels": ([vp, vp], ctypes.c_int),
@@ -296,6 +297,18 @@ class Graph:
     def count_fe(self, root: Optional[int] = None, threshold: float = 0.7, stream=None):
         """Algorithm CETC-Seq-FE: (count, whether the forward count ran)."""
         return tc_count_fe(self.handle, 0 if root is None else root, threshold, stream)
+
+    def relabel_degree(self, stream=None):
+        """Degree ordering (see tc_graph_relabel_degree): (new Graph, old_of_new)."""
+        out = ctypes.c_void_p()
+        perm = np.empty(max(self.n, 1), dtype=np.uint32)
+        _check(load_library().tc_graph_relabel_degree(
+            self.handle, _stream_handle(stream), ctypes.byref(out),
+            perm.ctypes.data_as(ctypes.c_void_p)), "tc_graph_relabel_degree")
+        g = Graph.__new__(Graph)
+        g.handle = out.value
+        g.n, g.m, g.d_max = tc_graph_info(g.handle)
+        return g, perm[: self.n].copy()
 
     def max_degree_vertex(self) -> int:
         return tc_max_degree_vertex(self.handle)

@@ -231,6 +231,9 @@ __global__ void k_maxdeg_vertex(const unsigned long long* __restrict__ row_ptr, 
   if (lane_id() == 0 && best != 0xFFFFFFFFu) atomicMin(vmin, best);
 }
 
+}  // namespace
+
+// Bits of a vertex id below n (at least 1).
 int key_bits(uint32_t n) {
   if (n <= 2) return 1;
   uint32_t x = n - 1;
@@ -242,7 +245,37 @@ int key_bits(uint32_t n) {
   return b;
 }
 
-}  // namespace
+
+tc_status sort_keys(unsigned long long** keys, unsigned long long** tmp, uint64_t N, int bits,
+                    cudaStream_t st) {
+  if (N == 0) return TC_OK;
+  const uint64_t nb = (N + kSortTile - 1) / kSortTile;
+  if (nb > 0x7FFFFFFFull) return TC_ERR_OVERFLOW;
+  const uint64_t hcount = (uint64_t)kRadix * nb;
+  uint32_t* hist = nullptr;
+  unsigned long long* hoff = nullptr;
+  ScanScratch ss;
+  ss.capacity = scan_scratch_entries(hcount + 1);
+  tc_status status = TC_OK;
+  if (cudaMalloc(&hist, sizeof(uint32_t) * hcount) != cudaSuccess ||
+      cudaMalloc(&hoff, sizeof(unsigned long long) * (hcount + 1)) != cudaSuccess ||
+      cudaMalloc(&ss.sums, sizeof(unsigned long long) * ss.capacity) != cudaSuccess)
+    status = TC_ERR_OOM;
+  for (int shift = 0; shift < bits && status == TC_OK; shift += kRadixBits) {
+    k_radix_hist<<<(unsigned)nb, kSortBlock, 0, st>>>(*keys, N, shift, (uint32_t)nb, hist); TC_LAUNCHED();
+    status = exclusive_scan_u32(hist, hoff, hcount, ss, st);
+    if (status != TC_OK) break;
+    k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, st>>>(*keys, *tmp, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
+    unsigned long long* t = *keys;
+    *keys = *tmp;
+    *tmp = t;
+  }
+  if (status == TC_OK && cudaStreamSynchronize(st) != cudaSuccess) status = TC_ERR_CUDA;
+  cudaFree(hist);
+  cudaFree(hoff);
+  cudaFree(ss.sums);
+  return status;
+}
 
 tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
                     cudaStream_t st, const EdgeGroups* groups) {

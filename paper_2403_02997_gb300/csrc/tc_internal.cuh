@@ -157,6 +157,12 @@ struct EdgeGroups {
 tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, uint64_t E,
                     cudaStream_t st, const EdgeGroups* groups = nullptr);
 tc_status run_bfs(tc_graph* g, uint32_t root, cudaStream_t st);
+// Stable LSD radix sort of N uint64 keys below 2^bits (8-bit digits).  The
+// sorted keys end in *keys; *tmp (N entries) is scratch, and the two pointers
+// may come back swapped.  Synchronises `st`.
+tc_status sort_keys(unsigned long long** keys, unsigned long long** tmp, uint64_t N, int bits,
+                    cudaStream_t st);
+int key_bits(uint32_t n);
 // BFS from the k roots already stored in queue_a (all at level 0, level[] set
 // to -1 elsewhere by the caller), then the restart rule.
 tc_status run_bfs_from_queue(tc_graph* g, uint64_t k, cudaStream_t st);

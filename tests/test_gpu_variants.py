@@ -136,3 +136,47 @@ def test_split_closed_form_complete():
         assert (st["c1"], st["c2"]) == (comb(19, 2), 3 * comb(19, 3))
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("gi", [0, 1, 3, 4, 6, 7, 9])
+def test_degree_relabel_cetc_d_and_sd(gi):
+    """tc_graph_relabel_degree against the oracle's degree ordering: the same
+    permutation and CSR; on the new graph tc_count (CETC-Seq-D) and
+    tc_count_split (CETC-Seq-SD) match the oracle's CETC on the relabelled
+    edges (count, c1 / c2, levels, cover set) and the original count."""
+    name, (n, s, d), _ = GRAPHS[gi]
+    rp, col = oracle.build_csr(n, s, d)
+    order = oracle.degree_order(rp)
+    s2, d2 = oracle.relabel_edges(order, s, d)
+    ref = oracle.count(n, s2, d2, 0, want_cover=True)
+    g = tc.Graph(s, d, n)
+    try:
+        g2, perm = g.relabel_degree()
+        try:
+            assert np.array_equal(perm, order)
+            rp2, col2 = g2.csr()
+            assert np.array_equal(rp2.astype(np.int64), ref["row_ptr"])
+            assert np.array_equal(col2, ref["col"])
+            assert g2.max_degree_vertex() == 0 or g2.m == 0
+            assert g2.count(0) == ref["T"] == oracle.forward(rp, col)
+            st = g2.stats()
+            assert (st["c1"], st["c2"], st["num_cover"]) == (ref["c1"], ref["c2"], ref["num_cover"])
+            assert np.array_equal(g2.levels(), ref["level"])
+            u, v = g2.cover_edges()
+            o = np.lexsort((v, u))
+            assert np.array_equal(u[o], ref["cover_u"]) and np.array_equal(v[o], ref["cover_v"])
+            assert g2.count_split(0) == ref["T"]
+        finally:
+            g2.close()
+    finally:
+        g.close()
+
+
+def test_relabel_empty():
+    g = tc.Graph(np.zeros(0, np.uint32), np.zeros(0, np.uint32), 4)
+    try:
+        g2, perm = g.relabel_degree()
+        assert perm.tolist() == [0, 1, 2, 3] and g2.m == 0 and g2.count(0) == 0
+        g2.close()
+    finally:
+        g.close()

@@ -417,3 +417,39 @@ def test_split_disconnected():
     g = graphs.relabel(graphs.disjoint_union(*parts), 9)
     for root in range(0, g[0], 7):
         assert _split(g, root)["T"] == comb(6, 3) + 6 + 1 + 0 + 2 * 2 * 3 + 0
+
+
+# --------------------------------------------------------------------------
+# Degree ordering (Algorithms CETC-Seq-D / CETC-Seq-SD)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("family,seed", [("er", 3), ("rmat", 7), ("wheel", 0), ("union", 1)])
+def test_degree_order(family, seed):
+    if family == "er":
+        n = 800
+        s, d = gen.er_edges(n, 6000, seed)
+    elif family == "rmat":
+        n = 1 << 10
+        s, d = gen.rmat_edges(10, 16, seed)
+    elif family == "wheel":
+        n, s, d = graphs.wheel(11)
+    else:
+        n, s, d = graphs.relabel(graphs.disjoint_union(graphs.complete(6), graphs.wheel(9),
+                                                       graphs.path(5)), seed)
+    rp, col = oracle.build_csr(n, s, d)
+    deg = np.diff(rp)
+    order = oracle.degree_order(rp)
+    # the definition, restated with Python's sort
+    assert order.tolist() == sorted(range(n), key=lambda v: (-int(deg[v]), v))
+    assert np.all(np.diff(deg[order]) <= 0)
+    s2, d2 = oracle.relabel_edges(order, s, d)
+    rp2, col2 = oracle.build_csr(n, s2, d2)
+    assert np.array_equal(np.diff(rp2), deg[order])
+    # relabelling keeps the count; the CETC count on the new graph (CETC-Seq-D)
+    # and the split count on it (CETC-Seq-SD) agree with Forward
+    f = oracle.forward(rp, col)
+    assert oracle.forward(rp2, col2) == f
+    lv2 = oracle.bfs_levels(rp2, col2, 0)
+    assert oracle.cetc(rp2, col2, lv2)["T"] == f == oracle.cetc_split(rp2, col2, lv2)["T"]
+    if family == "wheel":
+        assert order[0] == 0  # the hub
