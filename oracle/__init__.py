@@ -66,6 +66,9 @@ def _load():
         lib.orc_triples.argtypes = [ctypes.c_uint32, _u8p]
         lib.orc_forward.restype = ctypes.c_uint64
         lib.orc_forward.argtypes = [ctypes.c_uint32, _i64p, _u32p]
+        lib.orc_list_triangles.restype = ctypes.c_uint64
+        lib.orc_list_triangles.argtypes = [ctypes.c_uint32, _i64p, _u32p, _u32p, ctypes.c_uint64,
+                                           _u64p]
         lib.orc_cetc_split.restype = ctypes.c_uint64
         lib.orc_cetc_split.argtypes = [ctypes.c_uint32, _i64p, _u32p, _i32p, _u64p]
         _lib = lib
@@ -188,6 +191,18 @@ def cetc_split(row_ptr, col, level) -> dict:
     T = _load().orc_cetc_split(n, _p(row_ptr, _i64p), _p(col, _u32p), _p(level, _i32p),
                                _p(out, _u64p))
     return dict(T=int(T), T0=int(out[0]), T1=int(out[1]))
+
+
+def list_triangles(row_ptr, col):
+    """Every triangle as a row (a, b, c), a < b < c, in increasing order, and the
+    per-vertex triangle counts."""
+    n = row_ptr.size - 1
+    lib = _load()
+    vcount = np.zeros(max(n, 1), dtype=np.uint64)
+    T = lib.orc_list_triangles(n, _p(row_ptr, _i64p), _p(col, _u32p), None, 0, _p(vcount, _u64p))
+    tri = np.zeros((max(int(T), 1), 3), dtype=np.uint32)
+    lib.orc_list_triangles(n, _p(row_ptr, _i64p), _p(col, _u32p), _p(tri, _u32p), T, None)
+    return tri[: int(T)], vcount[:n]
 
 
 def degree_order(row_ptr) -> np.ndarray:

@@ -431,3 +431,49 @@ uint64_t orc_cetc_split(uint32_t n, const int64_t* row_ptr, const uint32_t* col,
   out[1] = t1;
   return t0 + t1;
 }
+
+/*
+ * Triangle listing (Section "Introduction": listing and per-vertex counts feed
+ * k-truss and clustering coefficients).  Every triangle {a, b, c}, a < b < c,
+ * exactly once: for each a, each b in N(a) above a, each c in N(a) ∩ N(b)
+ * above b (two-pointer merge).  Writes up to `cap` triples (a, b, c) to `out`
+ * in increasing (a, b, c) order and adds, for every triangle, 1 to vcount[a],
+ * vcount[b] and vcount[c] (vcount may be NULL).  Returns the number of
+ * triangles.
+ */
+uint64_t orc_list_triangles(uint32_t n, const int64_t* row_ptr, const uint32_t* col,
+                            uint32_t* out, uint64_t cap, uint64_t* vcount) {
+  uint64_t t = 0;
+  for (uint32_t a = 0; a < n; ++a) {
+    for (int64_t j = row_ptr[a]; j < row_ptr[a + 1]; ++j) {
+      const uint32_t b = col[j];
+      if (b <= a) continue;
+      int64_t x = row_ptr[a], y = row_ptr[b];
+      while (x < row_ptr[a + 1] && y < row_ptr[b + 1]) {
+        if (col[x] < col[y]) {
+          ++x;
+        } else if (col[x] > col[y]) {
+          ++y;
+        } else {
+          const uint32_t c = col[x];
+          if (c > b) {
+            if (out && t < cap) {
+              out[3 * t] = a;
+              out[3 * t + 1] = b;
+              out[3 * t + 2] = c;
+            }
+            if (vcount) {
+              ++vcount[a];
+              ++vcount[b];
+              ++vcount[c];
+            }
+            ++t;
+          }
+          ++x;
+          ++y;
+        }
+      }
+    }
+  }
+  return t;
+}

@@ -453,3 +453,36 @@ def test_degree_order(family, seed):
     assert oracle.cetc(rp2, col2, lv2)["T"] == f == oracle.cetc_split(rp2, col2, lv2)["T"]
     if family == "wheel":
         assert order[0] == 0  # the hub
+
+
+# --------------------------------------------------------------------------
+# Triangle listing and per-vertex counts
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_listing_against_matrix_and_brute_force(seed):
+    """Per-vertex counts = diag(A^3) / 2 (an exact int64 matrix product); the
+    list = the brute-force set of pairwise adjacent triples; |list| = Forward."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 60))
+    m = int(rng.integers(0, n * 4))
+    s = rng.integers(0, n, m).astype(np.uint32)
+    d = rng.integers(0, n, m).astype(np.uint32)
+    rp, col = oracle.build_csr(n, s, d)
+    tri, vc = oracle.list_triangles(rp, col)
+    a = oracle.adjacency_matrix(n, s, d).astype(np.int64)
+    assert np.array_equal(vc.astype(np.int64), np.diag(a @ a @ a) // 2)
+    brute = [t for t in itertools.combinations(range(n), 3)
+             if a[t[0], t[1]] and a[t[1], t[2]] and a[t[0], t[2]]]
+    assert [tuple(r) for r in tri.tolist()] == brute
+    assert len(brute) == oracle.forward(rp, col)
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 10])
+def test_listing_closed_forms(n):
+    rp, col = oracle.build_csr(*graphs.complete(n))
+    tri, vc = oracle.list_triangles(rp, col)
+    assert len(tri) == comb(n, 3) and np.all(vc == comb(n - 1, 2))
+    rp, col = oracle.build_csr(*graphs.wheel(n + 2))
+    tri, vc = oracle.list_triangles(rp, col)
+    assert vc[0] == n + 1 and np.all(vc[1:] == 2)
