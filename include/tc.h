@@ -107,6 +107,25 @@ tc_status tc_graph_info(const tc_graph* g, uint32_t* n, uint64_t* m, uint32_t* d
 tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count);
 
 /*
+ * Triangle listing and per-vertex triangle counts from the cover-edge count
+ * (the Introduction names k-truss and clustering coefficients as their users).
+ * The count runs as tc_count with root `root`; every triangle, found once at
+ * its cover edge {u, v} (u < v, L(u) == L(v)) with apex w under Algorithm
+ * CETC-Seq's rule, is also
+ *   - written to `triangles` (device, 3 x capacity uint32) as (u, v, w), in an
+ *     unspecified order, while fewer than `capacity` have been written;
+ *   - counted in vertex_counts[u], [v] and [w] (device, n uint64, zeroed by the
+ *     call; the number of triangles through each vertex).
+ * Either output may be NULL.  *count = all triangles; *written = the triples
+ * stored (min(count, capacity); may be NULL).  A count larger than capacity is
+ * not an error: call again with capacity >= count for the full list.  Levels,
+ * cover edges and statistics read as after tc_count.  Errors as tc_count.
+ */
+tc_status tc_list_triangles(tc_graph* g, uint32_t root, void* stream, uint32_t* triangles,
+                            uint64_t capacity, uint64_t* vertex_counts, uint64_t* count,
+                            uint64_t* written);
+
+/*
  * Algorithm CETC-Seq-S (Section "CETC Split Triangle Counting").  BFS levels
  * from `root` as in tc_count; the edges then split into G0, the horizontal
  * edges, and G1, the edges between levels.  T0 = the triangles of G0 by

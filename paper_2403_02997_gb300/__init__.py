@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "tc_count_many": ([P(vp), P(u32), ctypes.c_size_t, vp, P(u64)], ctypes.c_int),
         "tc_count_split": ([vp, u32, vp, P(u64)], ctypes.c_int),
         "tc_graph_relabel_degree": ([vp, vp, P(vp), vp], ctypes.c_int),
+        "tc_list_triangles": ([vp, u32, vp, vp, u64, vp, P(u64), P(u64)], ctypes.c_int),
         "tc_count_forward": ([vp, vp, P(u64)], ctypes.c_int),
         "tc_count_fe": ([vp, u32, ctypes.c_float, vp, P(u64), P(ctypes.c_int)], ctypes.c_int),
         "tc_get_levels": ([vp, vp], ctypes.c_int),
@@ -297,6 +298,29 @@ class Graph:
     def count_fe(self, root: Optional[int] = None, threshold: float = 0.7, stream=None):
         """Algorithm CETC-Seq-FE: (count, whether the forward count ran)."""
         return tc_count_fe(self.handle, 0 if root is None else root, threshold, stream)
+
+    def list_triangles(self, root: Optional[int] = None, capacity: Optional[int] = None,
+                       vertex_counts: bool = True, stream=None):
+        """Triangle listing (see tc_list_triangles) into torch device tensors.
+
+        Returns (count, triangles as an int64 (written, 3) numpy array of
+        (u, v, w), per-vertex counts as a uint64 numpy array or None).  With
+        capacity None the count runs once first to size the list."""
+        import torch
+        root = 0 if root is None else root
+        if capacity is None:
+            capacity = self.count(root, stream)
+        tri = torch.empty((max(int(capacity), 1), 3), dtype=torch.int32, device="cuda")
+        vc = torch.empty(max(self.n, 1), dtype=torch.int64, device="cuda") if vertex_counts else None
+        c, w = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load_library().tc_list_triangles(
+            self.handle, root, _stream_handle(stream), ctypes.c_void_p(tri.data_ptr()),
+            int(capacity), ctypes.c_void_p(vc.data_ptr()) if vc is not None else None,
+            ctypes.byref(c), ctypes.byref(w)), "tc_list_triangles")
+        torch.cuda.synchronize()
+        trip = tri[: w.value].cpu().numpy().view(np.uint32).astype(np.int64)
+        counts = vc[: self.n].cpu().numpy().view(np.uint64) if vc is not None else None
+        return int(c.value), trip, counts
 
     def relabel_degree(self, stream=None):
         """Degree ordering (see tc_graph_relabel_degree): (new Graph, old_of_new)."""

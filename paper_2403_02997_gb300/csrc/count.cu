@@ -97,6 +97,36 @@ __device__ __forceinline__ void flush_tally(Tally tl, DevCounters* ctr) {
   }
 }
 
+// Triangle emission of a listing count.  Every triangle is found once, at its
+// cover edge {a, b} (a < b) with apex w.
+struct Emit {
+  uint32_t* tri;               // triples (a, b, w); NULL: no list
+  unsigned long long cap;      // triples that fit
+  unsigned long long* cursor;  // triangles found so far (device)
+  unsigned long long* vcount;  // per-vertex counts; NULL: none
+  uint32_t a, b;               // the cover edge of the hits passed to put()
+  // Warp-collective (all 32 lanes, converged): lane hits `hit` (0 or 1) with
+  // apex w.  One cursor atomic per call; a and b's counts are added per edge
+  // by the caller.
+  __device__ __forceinline__ void put(uint32_t hit, uint32_t w) const {
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (!m) return;
+    if (vcount && hit) atomicAdd(&vcount[w], 1ull);
+    if (!tri) return;
+    const unsigned lane = lane_id(), leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+    if (hit && pos < cap) {
+      tri[3 * pos] = a;
+      tri[3 * pos + 1] = b;
+      tri[3 * pos + 2] = w;
+    }
+  }
+};
+
+template <bool kEmit>
 __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long* __restrict__ row_ptr,
                                                        const uint32_t* __restrict__ col,
                                                        const int32_t* __restrict__ level, uint32_t n,
@@ -109,7 +139,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                                                        const unsigned long long* __restrict__ voff,
                                                        uint32_t nb,
                                                        unsigned long long* __restrict__ gcount,
-                                                       DevCounters* ctr) {
+                                                       DevCounters* ctr, Emit em) {
   __shared__ uint32_t s_lo, s_hi, s_g0, s_g1;
   Tally tl;
   // batch mode: counts of the inline merges go to their graph, one atomic per
@@ -165,6 +195,37 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                   ++x;
                 } else {
                   ++y;
+                }
+              }
+              if (kEmit && here) {
+                // the same merge again, writing this edge's triangles to the
+                // slots reserved for them
+                unsigned long long pos = em.tri ? atomicAdd(em.cursor, (unsigned long long)here) : 0;
+                if (em.vcount) {
+                  atomicAdd(&em.vcount[u], (unsigned long long)here);
+                  atomicAdd(&em.vcount[v], (unsigned long long)here);
+                }
+                x = bu;
+                y = bv;
+                while (x < eu && y < ev) {
+                  const uint32_t a = col[x], c = col[y];
+                  if (a == c) {
+                    if (level[a] != lu || v < a) {
+                      if (em.tri && pos < em.cap) {
+                        em.tri[3 * pos] = u;
+                        em.tri[3 * pos + 1] = v;
+                        em.tri[3 * pos + 2] = a;
+                      }
+                      ++pos;
+                      if (em.vcount) atomicAdd(&em.vcount[a], 1ull);
+                    }
+                    ++x;
+                    ++y;
+                  } else if (a < c) {
+                    ++x;
+                  } else {
+                    ++y;
+                  }
                 }
               }
               if (nb && here) {
@@ -506,10 +567,11 @@ __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo ck, uint32_t sorted_l
 // past its part (read again by the next chunk).  In the last step, whole rows
 // of 32 ids past end or above hi are skipped and the rest is masked per id.  A
 // segment is one row's part: shorter than n < 2^31.
-template <bool kBounded, bool kSorted>
+template <bool kBounded, bool kSorted, bool kEmit>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, const unsigned long long cur, const unsigned long long end,
-    const uint32_t hi, const Cuckoo ck, const uint32_t sorted_len, uint32_t& hits) {
+    const uint32_t hi, const Cuckoo ck, const uint32_t sorted_len, const Emit& em,
+    uint32_t& hits) {
   if (cur >= end) return end;
   const uint32_t lane = lane_id();
   const uint32_t* p = arr + cur + lane;
@@ -525,7 +587,11 @@ __device__ __forceinline__ unsigned long long stream_segment(
 #pragma unroll
       for (int t = 0; t < 4; ++t) wn[t] = (int)len > 128 + 32 * t ? __ldg(p + 128 + 32 * t) : kEmpty;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) hits += chunk_hit<kSorted>(ck, sorted_len, w[t]);
+      for (int t = 0; t < 4; ++t) {
+        const uint32_t hit = chunk_hit<kSorted>(ck, sorted_len, w[t]);
+        hits += hit;
+        if (kEmit) em.put(hit, w[t]);
+      }
     } else {
       // ids ascend with 32 t + lane, so the ids taken (before end, at most hi)
       // form a prefix of the step: stop at the first row of 32 with none
@@ -536,7 +602,9 @@ __device__ __forceinline__ unsigned long long stream_segment(
         const unsigned m = __ballot_sync(0xffffffffu, in);
         if (!m) break;
         taken += __popc(m);
-        hits += (uint32_t)in & chunk_hit<kSorted>(ck, sorted_len, w[t]);
+        const uint32_t hit = (uint32_t)in & chunk_hit<kSorted>(ck, sorted_len, w[t]);
+        hits += hit;
+        if (kEmit) em.put(hit, w[t]);
       }
       // the new cursor follows the ids taken
       return (unsigned long long)(p - lane - arr) + taken;
@@ -556,18 +624,18 @@ struct EdgePass {
 
 // Both segments of one cover edge for one chunk.  A segment is part of one row,
 // so it holds fewer than n < 2^31 ids (stream_segment's length is an int).
-template <bool kBounded, bool kSorted>
+template <bool kBounded, bool kSorted, bool kEmit>
 __device__ __forceinline__ EdgePass stream_edge(const uint32_t* __restrict__ lcol,
                                                 unsigned long long a, unsigned long long ae,
                                                 unsigned long long b, unsigned long long be,
                                                 uint32_t hi, const Cuckoo ck,
-                                                uint32_t sorted_len) {
+                                                uint32_t sorted_len, const Emit& em) {
   EdgePass r{a, b, 0, 0};
 #pragma unroll 1
   for (int part = 0; part < 2; ++part) {  // one copy of the loop for both segments
     uint32_t hits = 0;
-    const unsigned long long cur = stream_segment<kBounded, kSorted>(
-        lcol, part ? b : a, part ? be : ae, hi, ck, sorted_len, hits);
+    const unsigned long long cur = stream_segment<kBounded, kSorted, kEmit>(
+        lcol, part ? b : a, part ? be : ae, hi, ck, sorted_len, em, hits);
     if (part) {
       r.b = cur;
       r.c2c = hits;
@@ -583,14 +651,15 @@ __device__ __forceinline__ EdgePass stream_edge(const uint32_t* __restrict__ lco
 // weigh on the registers of the hot loop.  Arguments and result go by value:
 // nothing of the caller's has its address taken (which would put it in local
 // memory).
+template <bool kEmit>
 __device__ __noinline__ EdgePass stream_edge_sorted(const uint32_t* __restrict__ lcol,
                                                     unsigned long long a, unsigned long long ae,
                                                     unsigned long long b, unsigned long long be,
                                                     bool bounded, uint32_t hi,
-                                                    uint32_t sorted_len) {
+                                                    uint32_t sorted_len, const Emit em) {
   const Cuckoo none{0};
-  if (bounded) return stream_edge<true, true>(lcol, a, ae, b, be, hi, none, sorted_len);
-  return stream_edge<false, true>(lcol, a, ae, b, be, hi, none, sorted_len);
+  if (bounded) return stream_edge<true, true, kEmit>(lcol, a, ae, b, be, hi, none, sorted_len, em);
+  return stream_edge<false, true, kEmit>(lcol, a, ae, b, be, hi, none, sorted_len, em);
 }
 
 // First index in arr[a, b) (sorted) with arr[i] >= t.
@@ -621,14 +690,14 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // (kPlain = true): the table is tcol[tb[h], te[h]) and the streamer streams the
 // one segment scol[sb[x], se[x]); hits are tallied as c1, or as c2' when
 // plain_as_c2 is set.
-template <int kThreads, bool kPlain>
+template <int kThreads, bool kPlain, bool kEmit>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const HashRows rows, const unsigned long long* __restrict__ ooff,
     const uint32_t* __restrict__ ostream, const unsigned long long* __restrict__ ioff,
     const uint32_t* __restrict__ item_owner, unsigned long long nitems, uint32_t chunk,
     uint32_t per_item, uint32_t force_sorted, uint32_t plain_as_c2,
     const unsigned long long* __restrict__ voff, uint32_t nb,
-    unsigned long long* __restrict__ gcount, DevCounters* ctr) {
+    unsigned long long* __restrict__ gcount, DevCounters* ctr, Emit em) {
   const unsigned long long* __restrict__ tb = rows.tb;
   const unsigned long long* __restrict__ te = rows.te;
   const uint32_t* __restrict__ col = rows.tcol;
@@ -638,6 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
   // cursors of the slice's edges (edges_per_item <= kThreads)
   __shared__ unsigned long long s_a[kThreads], s_ae[kThreads];
   __shared__ unsigned long long s_b[kThreads], s_be[kThreads];
+  __shared__ uint32_t s_x[kEmit ? kThreads : 1];  // streamers (listing only)
   const unsigned lane = lane_id();
   Tally tl;
   for (;;) {
@@ -654,6 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x) {
       const uint32_t x = ostream[eb + i];
       const unsigned long long sp = rows.se[x];
+      if (kEmit) s_x[i] = x;
       s_a[i] = rows.sb[x];
       s_ae[i] = sp;
       if (kPlain) {
@@ -696,12 +767,25 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         if (i >= ne) break;
         const unsigned long long a = s_a[i], b = s_b[i];
         const unsigned long long ae = s_ae[i], be = s_be[i];
+        Emit ed = em;
+        if (kEmit) {
+          const uint32_t x = s_x[i];
+          ed.a = min(h, x);
+          ed.b = max(h, x);
+        }
         EdgePass r;
         if (!sorted) {
-          if (bounded) r = stream_edge<true, false>(lcol, a, ae, b, be, hi_id, ck, entries);
-          else r = stream_edge<false, false>(lcol, a, ae, b, be, hi_id, ck, entries);
+          if (bounded) r = stream_edge<true, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
+          else r = stream_edge<false, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
         } else {
-          r = stream_edge_sorted(lcol, a, ae, b, be, bounded, hi_id, entries);
+          r = stream_edge_sorted<kEmit>(lcol, a, ae, b, be, bounded, hi_id, entries, ed);
+        }
+        if (kEmit && em.vcount) {  // the cover edge's endpoints, once per edge and chunk
+          const unsigned long long eh = warp_sum((unsigned long long)(r.c1 + r.c2c));
+          if (lane == 0 && eh) {
+            atomicAdd(&em.vcount[h], eh);
+            atomicAdd(&em.vcount[s_x[i]], eh);
+          }
         }
         if (lane == 0) {
           s_a[i] = r.a;
@@ -957,10 +1041,10 @@ tc_status run_level_split(tc_graph* g, cudaStream_t st) {
 // whose per-owner counts are in g->ocount and their exclusive scan in g->ooff:
 // bucket the streamers by owner, slice each owner's bucket into work items of
 // edges_per_item, and launch k_owner_hash over the items.
-template <bool kPlain>
+template <bool kPlain, bool kEmit = false>
 tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows& rows,
                          uint32_t plain_as_c2, const unsigned long long* voff, uint32_t nb,
-                         unsigned long long* gcount, cudaStream_t st) {
+                         unsigned long long* gcount, cudaStream_t st, const Emit& em = Emit{}) {
   const uint32_t n = g->n;
   const int sms = num_sms();
   TC_CUDA_TRY(cudaMemsetAsync(g->ofill, 0, sizeof(uint32_t) * n, st));
@@ -990,8 +1074,8 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   const size_t smem = owner_hash_smem(chunk);
   const bool wide = g->params.hash_block == 2 * kHashBlock;
   const int threads = wide ? 2 * kHashBlock : kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, kPlain>
-                          : (const void*)k_owner_hash<kHashBlock, kPlain>;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, kPlain, kEmit>
+                          : (const void*)k_owner_hash<kHashBlock, kPlain, kEmit>;
   TC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -1001,13 +1085,13 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
   const uint32_t force_sorted = g->params.sorted_lookup ? 1u : 0u;
   if (wide)
-    k_owner_hash<2 * kHashBlock, kPlain><<<grid, threads, smem, st>>>(
+    k_owner_hash<2 * kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
         rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr);
+        plain_as_c2, voff, nb, gcount, g->ctr, em);
   else
-    k_owner_hash<kHashBlock, kPlain><<<grid, threads, smem, st>>>(
+    k_owner_hash<kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
         rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr);
+        plain_as_c2, voff, nb, gcount, g->ctr, em);
   TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;
@@ -1026,8 +1110,8 @@ tc_status scan_owners(tc_graph* g, cudaStream_t st, unsigned long long* nlarge) 
 
 tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
   const bool wide = hash_block == 2 * kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, false>
-                          : (const void*)k_owner_hash<kHashBlock, false>;
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, false, false>
+                          : (const void*)k_owner_hash<kHashBlock, false, false>;
   cudaFuncAttributes fa;
   TC_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
   int dev = 0, optin = 0;
@@ -1047,10 +1131,10 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   }
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   const uint32_t small_max = g->params.small_max_degree;
-  k_cover<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+  k_cover<false><<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
       g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
       g->params.medium_max_degree > kMediumCap ? kMediumCap : g->params.medium_max_degree,
-      g->medium, g->voff, g->batch_k, g->gcount, g->ctr); TC_LAUNCHED();
+      g->medium, g->voff, g->batch_k, g->gcount, g->ctr, Emit{}); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
   unsigned long long nlarge = 0;
@@ -1170,6 +1254,26 @@ tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long*
   TC_CUDA_TRY(cudaStreamSynchronize(st));
   *num_cover = g->ctr_host->num_cover;
   return TC_OK;
+}
+
+tc_status run_cover_and_list(tc_graph* g, const EmitSink& sink, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const int sms = num_sms();
+  TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
+  if (g->nnz == 0) return TC_OK;
+  const Emit em{sink.tri, sink.cap, &g->ctr->listed, sink.vcount, 0, 0};
+  TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
+  k_cover<true><<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
+      g->row_ptr, g->col, g->level, n, g->nnz, g->params.small_max_degree, g->cover, g->large,
+      g->ocount, 0, g->medium, nullptr, 0, nullptr, g->ctr, em); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  unsigned long long nlarge = 0;
+  TC_TRY(scan_owners(g, st, &nlarge));
+  if (nlarge == 0) return TC_OK;
+  TC_TRY(run_level_split(g, st));
+  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->row_ptr, g->lsplit, g->lcol};
+  return run_owner_pass<false, true>(g, nlarge, rows, 0, nullptr, 0, nullptr, st, em);
 }
 
 }  // namespace tc

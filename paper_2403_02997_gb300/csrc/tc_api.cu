@@ -285,6 +285,32 @@ tc_status tc_count(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
   return TC_OK;
 }
 
+tc_status tc_list_triangles(tc_graph* g, uint32_t root, void* stream, uint32_t* triangles,
+                            uint64_t capacity, uint64_t* vertex_counts, uint64_t* count,
+                            uint64_t* written) {
+  if (written) *written = 0;
+  if (g && vertex_counts && g->n)
+    TC_CUDA_TRY(cudaMemsetAsync(vertex_counts, 0, sizeof(uint64_t) * g->n,
+                                static_cast<cudaStream_t>(stream)));
+  tc_status s;
+  if (!begin_count(g, root, true, count, &s)) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t launches0 = g_launches;
+  TC_CUDA_TRY(cudaEventRecord(g->ev[0], st));
+  TC_TRY(run_bfs(g, root, st));
+  TC_CUDA_TRY(cudaEventRecord(g->ev[1], st));
+  const EmitSink sink{triangles, triangles ? capacity : 0,
+                      reinterpret_cast<unsigned long long*>(vertex_counts)};
+  TC_TRY(run_cover_and_list(g, sink, st));
+  TC_TRY(finish_count(g, st, count, launches0));
+  // every counted triangle was emitted exactly once
+  if (triangles && g->ctr_host->listed != g->ctr_host->tri) return TC_ERR_CUDA;
+  if (written) *written = triangles ? (*count < capacity ? *count : capacity) : 0;
+  g->counted = true;
+  g->last_root = root;
+  return TC_OK;
+}
+
 tc_status tc_count_split(tc_graph* g, uint32_t root, void* stream, uint64_t* count) {
   tc_status s;
   if (!begin_count(g, root, true, count, &s)) return s;

@@ -28,6 +28,7 @@ struct DevCounters {
   unsigned long long items;      // owner-hash work items
   unsigned long long item_cursor;// dynamic work counter
   unsigned long long unvisited;  // vertices still unvisited
+  unsigned long long listed;     // triangle listing: triangles found so far (output cursor)
   unsigned long long plen[3];    // persistent BFS: frontier lengths, one slot per level mod 3
   unsigned long long pedges[3];  // persistent BFS: degree sums of those frontiers
   unsigned int pmaxdeg[3];       // persistent BFS: largest degree in those frontiers
@@ -187,6 +188,17 @@ tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block);
 tc_status run_forward_count(tc_graph* g, cudaStream_t st);
 // Algorithm CETC-Seq-S after run_bfs: c1 = T1, c2 = 3 T0, tri = T0 + T1.
 tc_status run_split_count(tc_graph* g, cudaStream_t st);
+// Where a listing count puts its triangles: up to cap triples (u, v, w) in
+// tri[3 cap] (device; NULL: none) and per-vertex counts in vcount[n] (device,
+// zeroed by the caller; NULL: none).
+struct EmitSink {
+  uint32_t* tri;
+  unsigned long long cap;
+  unsigned long long* vcount;
+};
+// run_cover_and_count with every counted triangle also emitted to `sink`
+// (single graphs only; the medium bin is not used).
+tc_status run_cover_and_list(tc_graph* g, const EmitSink& sink, cudaStream_t st);
 // |S| after run_bfs (resets g->ctr).
 tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long* num_cover);
 

@@ -54,6 +54,7 @@ def test_host_side_argument_checks(lib):
     assert lib.tc_count_forward(None, None, None) == 1
     assert lib.tc_count_fe(None, 0, 0.7, None, None, None) == 1
     assert lib.tc_graph_relabel_degree(None, None, None, None) == 1
+    assert lib.tc_list_triangles(None, 0, None, None, 0, None, None, None) == 1
     assert lib.tc_count_many(None, None, 0, None, None) == 0
     assert lib.tc_graph_destroy(None) == 0
     p = tc.tc_params()

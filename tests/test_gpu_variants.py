@@ -180,3 +180,37 @@ def test_relabel_empty():
         g2.close()
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("pname", list(PARAMS))
+@pytest.mark.parametrize("gi", [0, 1, 3, 4, 6, 9])
+def test_triangle_listing(gi, pname):
+    """tc_list_triangles against the oracle's enumeration: the same set of
+    triangles (each once), per-vertex counts, each triple led by its cover edge
+    (u < v on one level); a capacity below the count keeps the count and
+    writes a subset."""
+    name, (n, s, d), root = GRAPHS[gi]
+    rp, col = oracle.build_csr(n, s, d)
+    if root == "maxdeg":
+        root = oracle.max_degree_root(rp)
+    tri_ref, vc_ref = oracle.list_triangles(rp, col)
+    lv = oracle.bfs_levels(rp, col, root)
+    g = tc.Graph(s, d, n)
+    try:
+        g.set_params(**PARAMS[pname])
+        T, tri, vc = g.list_triangles(root)
+        assert T == len(tri_ref) and len(tri) == T
+        assert np.all(tri[:, 0] < tri[:, 1]) and np.all(lv[tri[:, 0]] == lv[tri[:, 1]])
+        srt = np.sort(tri, axis=1)
+        srt = srt[np.lexsort((srt[:, 2], srt[:, 1], srt[:, 0]))]
+        assert np.array_equal(srt, tri_ref.astype(np.int64))
+        assert np.array_equal(vc, vc_ref)
+        if T > 3:
+            T2, part, none = g.list_triangles(root, capacity=T // 2, vertex_counts=False)
+            assert T2 == T and len(part) == T // 2 and none is None
+            ref_set = set(map(tuple, tri_ref.tolist()))
+            got = [tuple(sorted(t)) for t in part.tolist()]
+            assert len(set(got)) == len(got) and set(got) <= ref_set
+        assert g.count(root) == T  # the handle counts as before
+    finally:
+        g.close()
