@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
       if (j < e1) {
         const uint32_t u = row_of(row_ptr, lo, hi, j);
         const uint32_t v = col[j];
-        if (v > u) {
+        if (check_failed(v >= n, ctr)) {
+        } else if (v > u) {
           const int32_t lu = level[u];
           if (level[v] == lu) {
             is_cover = true;
@@ -463,11 +464,13 @@ __global__ void __launch_bounds__(kTileBlock) k_split_tile_write(
 
 __global__ void k_bucket(const uint2* __restrict__ large, unsigned long long count,
                          const unsigned long long* __restrict__ ooff, uint32_t* __restrict__ ofill,
-                         uint32_t* __restrict__ ostream) {
+                         uint32_t* __restrict__ ostream, uint32_t n, DevCounters* ctr) {
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const uint2 e = large[i];
+    if (check_failed(e.x >= n, ctr)) continue;
     const unsigned long long pos = ooff[e.x] + atomicAdd(&ofill[e.x], 1u);
+    if (check_failed(pos >= count || pos >= ooff[e.x + 1], ctr)) continue;
     ostream[pos] = e.y;
   }
 }
@@ -697,7 +700,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const uint32_t* __restrict__ item_owner, unsigned long long nitems, uint32_t chunk,
     uint32_t per_item, uint32_t force_sorted, uint32_t plain_as_c2,
     const unsigned long long* __restrict__ voff, uint32_t nb,
-    unsigned long long* __restrict__ gcount, DevCounters* ctr, Emit em) {
+    unsigned long long* __restrict__ gcount, DevCounters* ctr, Emit em, uint32_t n,
+    unsigned long long nnz_cap) {
   const unsigned long long* __restrict__ tb = rows.tb;
   const unsigned long long* __restrict__ te = rows.te;
   const uint32_t* __restrict__ col = rows.tcol;
@@ -716,15 +720,21 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const unsigned long long item = s_item;
     if (item >= nitems) break;
     const uint32_t h = item_owner[item];
+    if (check_failed(h >= n, ctr)) continue;  // block-uniform
     const unsigned long long hb = tb[h], he = te[h];
+    if (check_failed(hb > he || he > nnz_cap, ctr)) continue;
     const uint32_t chunks = (uint32_t)((he - hb + chunk - 1) / chunk);
     const unsigned long long eb = ooff[h] + (item - ioff[h]) * per_item;
     unsigned long long item_hits = 0;  // this thread's hits in this item (batch mode)
     const uint32_t ne = (uint32_t)min((unsigned long long)per_item, ooff[h + 1] - eb);
     for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x) {
       const uint32_t x = ostream[eb + i];
-      const unsigned long long sp = rows.se[x];
       if (kEmit) s_x[i] = x;
+      if (check_failed(x >= n, ctr)) {  // an empty edge instead
+        s_a[i] = s_ae[i] = s_b[i] = s_be[i] = 0;
+        continue;
+      }
+      const unsigned long long sp = rows.se[x];
       s_a[i] = rows.sb[x];
       s_ae[i] = sp;
       if (kPlain) {
@@ -735,6 +745,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         s_b[i] = lower_bound_u32(lcol, sp, xe, v + 1);
         s_be[i] = xe;
       }
+      if (check_failed(s_a[i] > s_ae[i] || s_ae[i] > nnz_cap || s_b[i] > s_be[i] ||
+                       s_be[i] > nnz_cap, ctr))
+        s_a[i] = s_ae[i] = s_b[i] = s_be[i] = 0;
     }
     for (uint32_t c = 0; c < chunks; ++c) {
       const unsigned long long cb = hb + (unsigned long long)c * chunk;
@@ -892,7 +905,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_forward_pairs(
       uint2 le = make_uint2(0, 0);
       if (j < e1) {
         const uint32_t x = row_of(obeg, lo, hi, j);
-        const uint32_t w = ocol[j];
+        const uint32_t w = check_failed(ocol[j] >= n, ctr) ? x : ocol[j];
         const unsigned long long bx = obeg[x], ex = obeg[x + 1];
         const unsigned long long bw = obeg[w], ew = obeg[w + 1];
         const unsigned long long dx = ex - bx, dw = ew - bw;
@@ -1049,7 +1062,7 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   const int sms = num_sms();
   TC_CUDA_TRY(cudaMemsetAsync(g->ofill, 0, sizeof(uint32_t) * n, st));
   k_bucket<<<grid_for(nlarge, 256, sms * 16), 256, 0, st>>>(g->large, nlarge, g->ooff, g->ofill,
-                                                           g->ostream); TC_LAUNCHED();
+                                                           g->ostream, n, g->ctr); TC_LAUNCHED();
   const uint32_t chunk = g->params.hash_chunk;
   const uint32_t per_item = g->params.edges_per_item;
   k_item_counts<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ocount, n, per_item, g->fdeg); TC_LAUNCHED();
@@ -1087,11 +1100,11 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   if (wide)
     k_owner_hash<2 * kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
         rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr, em);
+        plain_as_c2, voff, nb, gcount, g->ctr, em, n, g->nnz);
   else
     k_owner_hash<kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
         rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr, em);
+        plain_as_c2, voff, nb, gcount, g->ctr, em, n, g->nnz);
   TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;

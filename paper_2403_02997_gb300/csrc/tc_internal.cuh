@@ -12,7 +12,17 @@ constexpr int kWarp = 32;
 constexpr uint32_t kNoLevel = 0xFFFFFFFFu;  // level word of an unvisited vertex (-1)
 
 // Device-side error word values (bit flags, OR-ed by kernels).
-enum : uint32_t { kErrVertexRange = 1u, kErrTimeout = 2u, kErrOverflow = 4u };
+enum : uint32_t { kErrVertexRange = 1u, kErrTimeout = 2u, kErrOverflow = 4u, kErrBounds = 8u };
+
+// Checked builds (-DTC_CHECKED, the stand-in for a memory checker): kernels
+// test the preconditions of their data-dependent accesses, record a failure
+// in the error word (the count then returns TC_ERR_CUDA) and skip the access
+// instead of trapping.  In normal builds the checks compile away.
+#ifdef TC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 // Counters that kernels accumulate and the host reads back with one copy.
 struct DevCounters {
@@ -203,6 +213,17 @@ tc_status run_cover_and_list(tc_graph* g, const EmitSink& sink, cudaStream_t st)
 tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long* num_cover);
 
 // ---- device helpers -----------------------------------------------------
+
+// True (and the failure recorded) when `bad` holds in a checked build; always
+// false in a normal build.
+template <typename Counters>
+__device__ __forceinline__ bool check_failed(bool bad, Counters* ctr) {
+  if (kChecked && bad) {
+    atomicOr(&ctr->err, (unsigned)kErrBounds);
+    return true;
+  }
+  return false;
+}
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
