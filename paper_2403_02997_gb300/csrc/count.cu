@@ -31,6 +31,20 @@
 //                streams its segments of N(x), 128 ids per warp step, up to the
 //                chunk's largest id through it.
 // Per-thread counts are reduced by warp shuffles and one atomic per CTA.
+//
+// The same machinery serves the paper's variants and the listing:
+// k_g1_pairs       Algorithm CETC-Seq-S's T1: the cover edges with the
+//                  intersections of their G1 rows (the other-level parts of the
+//                  level-split rows);
+// k_orient, k_forward_pairs
+//                  Algorithm Forward's orientation by (degree, id) and its
+//                  pairs |A+(x) ∩ A+(w)| (CETC-Seq-S's T0 on G0, and the whole
+//                  graph for CETC-Seq-FE's forward branch); k_owner_hash's plain
+//                  instances intersect the pairs of both that are too long for
+//                  a thread's merge;
+// k_horizontal     |S|, for CETC-Seq-FE's covering ratio;
+// kEmit instances  of k_cover and k_owner_hash emit every triangle they count
+//                  (triangle listing and per-vertex counts).
 #include "tc_internal.cuh"
 
 namespace tc {
