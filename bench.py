@@ -279,14 +279,15 @@ class OracleSampler:
         self.rng = np.random.default_rng(seed)
         self.cores = max(1, int(cores or os.cpu_count() or 1))
 
-    def _edges(self, lv, us, vs):
+    def _edges(self, lv, us, vs) -> int:
+        """The oracle's count over the given cover edges, on self.cores threads."""
         if self.cores == 1 or us.size < 4 * self.cores:
-            self.o.cetc_edges(self.rp, self.col, lv, us, vs)
-            return
+            return self.o.cetc_edges(self.rp, self.col, lv, us, vs)["T"]
         from concurrent.futures import ThreadPoolExecutor
         parts = np.array_split(np.arange(us.size), self.cores)
         with ThreadPoolExecutor(self.cores) as ex:
-            list(ex.map(lambda ix: self.o.cetc_edges(self.rp, self.col, lv, us[ix], vs[ix]), parts))
+            return sum(r["T"] for r in ex.map(
+                lambda ix: self.o.cetc_edges(self.rp, self.col, lv, us[ix], vs[ix]), parts))
 
     def step(self) -> dict:
         t = time.perf_counter()
