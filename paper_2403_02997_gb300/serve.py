@@ -62,14 +62,40 @@ class Request:
         return self.done - self.arrival
 
 
-class Server:
-    def __init__(self, hbm_budget_bytes: int = 64 << 30, max_batch: int = 4096, params=None):
+class GpuBackend:
+    """Builds an admitted group as one device batch and counts it (the library's batch calls).
+
+    Builds run on one stream and counts on another, so a group builds while the previous one
+    counts.
+    """
+
+    def __init__(self, params=None):
         import torch
-        self.budget = int(hbm_budget_bytes)
-        self.max_batch = max_batch
         self.params = dict(params or {})
         self.build_stream = torch.cuda.Stream()
         self.count_stream = torch.cuda.Stream()
+
+    def build(self, group):
+        """One batch straight from the group's edge lists; returns (batch, roots)."""
+        b = tc.Batch.from_edges([(r.src, r.dst, r.n) for r in group], stream=self.build_stream)
+        if self.params:
+            b.set_params(**self.params)
+        md = b.max_degree_vertices(stream=self.build_stream)
+        return b, [md[i] if r.root is None else r.root for i, r in enumerate(group)]
+
+    def count(self, batch, roots):
+        return batch.count(roots, stream=self.count_stream)
+
+    def release(self, batch) -> None:
+        batch.close()
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, max_batch: int = 4096, params=None,
+                 backend=None):
+        self.budget = int(hbm_budget_bytes)
+        self.max_batch = max_batch
+        self.backend = backend if backend is not None else GpuBackend(params)
         self.lock = threading.Condition()
         self.pending: deque = deque()     # arrived, not admitted
         self.ready: List = []             # (request, graph, root) built, waiting for a batch
@@ -123,12 +149,7 @@ class Server:
                 continue
             try:
                 # one device build for the whole group: a batch straight from the edge lists
-                b = tc.Batch.from_edges([(r.src, r.dst, r.n) for r in group],
-                                        stream=self.build_stream)
-                if self.params:
-                    b.set_params(**self.params)
-                md = b.max_degree_vertices(stream=self.build_stream)
-                roots = [md[i] if r.root is None else r.root for i, r in enumerate(group)]
+                b, roots = self.backend.build(group)
                 with self.lock:
                     self.ready.append((group, b, roots))
                     self.lock.notify_all()
@@ -151,10 +172,10 @@ class Server:
                     return
                 reqs, b, roots = self.ready.pop(0)
             try:
-                counts, err = b.count(roots, stream=self.count_stream), None
+                counts, err = self.backend.count(b, roots), None
             except Exception as e:
                 counts, err = [None] * len(reqs), str(e)
-            b.close()
+            self.backend.release(b)
             now = time.perf_counter()
             for r, c in zip(reqs, counts):
                 r.count, r.error, r.done = c, err, now

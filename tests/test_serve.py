@@ -36,3 +36,77 @@ def test_results_alone_and_in_the_mix():
     assert srv.peak_used <= budget
     assert max(srv.batches) > 1          # requests were built and counted together
     assert res["p99_ms"] >= res["p50_ms"] > 0
+
+
+class OracleBackend:
+    """A host stand-in for the device (the oracle counts each graph), so the
+    serving loop's admission, grouping and answering run without a GPU."""
+
+    def __init__(self, delay=0.002, fail_build=False):
+        self.delay = delay
+        self.fail_build = fail_build
+        self.released = 0
+
+    def build(self, group):
+        import time
+        time.sleep(self.delay)
+        if self.fail_build:
+            raise RuntimeError("build failed")
+        return [(r.src, r.dst, r.n) for r in group], [r.root for r in group]
+
+    def count(self, batch, roots):
+        import time
+
+        import oracle
+        time.sleep(self.delay)
+        out = []
+        for s, d, n in batch:
+            rp, col = oracle.build_csr(n, s, d)
+            out.append(oracle.forward(rp, col))  # T does not depend on the root
+        return out
+
+    def release(self, batch):
+        self.released += 1
+
+
+def _pool(k=24):
+    specs = gen.batched_specs(k, master_seed=7, log2_min=6, log2_max=10)
+    return [(*sp.edges(), sp.n, None if sp.root == "maxdeg" else 0) for sp in specs]
+
+
+def test_admission_respects_budget_and_answers_everything():
+    import oracle
+    from paper_2403_02997_gb300 import serve
+    pool = _pool()
+    want = []
+    for s, d, n, _ in pool:
+        rp, col = oracle.build_csr(n, s, d)
+        want.append(oracle.forward(rp, col))
+    budget = 3 * max(serve.footprint_bytes(n, s.size) for s, _, n, _ in pool)
+    be = OracleBackend()
+    srv = serve.Server(hbm_budget_bytes=budget, max_batch=6, backend=be)
+    res = serve.run_arrivals(srv, pool, rate=20000.0, count=150, seed=2)
+    srv.close()
+    assert res["errors"] == 0 and len(srv.completed) == 150
+    for r in res["requests_list"]:
+        idx = [i for i, p in enumerate(pool) if p[0] is r.src][0]
+        assert r.count == want[idx]
+    assert 0 < srv.peak_used <= budget and srv.used == 0
+    assert max(srv.batches) > 1 and max(srv.batches) <= 6      # grouped, never above max_batch
+    assert be.released == len(srv.batches)
+    assert res["p99_ms"] >= res["p50_ms"] > 0
+
+
+def test_oversized_request_and_failed_build():
+    from paper_2403_02997_gb300 import serve
+    s, d, n, root = _pool(2)[1]
+    small = serve.footprint_bytes(n, s.size)
+    srv = serve.Server(hbm_budget_bytes=small - 1, backend=OracleBackend())
+    r = srv.submit(serve.Request(rid=0, src=s, dst=d, n=n))
+    assert r.event.is_set() and r.error and r.count is None
+    srv.close()
+    srv = serve.Server(hbm_budget_bytes=4 * small, backend=OracleBackend(fail_build=True))
+    r = srv.submit(serve.Request(rid=1, src=s, dst=d, n=n))
+    assert r.event.wait(10) and r.error == "build failed"
+    srv.close()
+    assert srv.used == 0
