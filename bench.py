@@ -60,6 +60,15 @@ def parse_args():
                    help="target seconds of oracle intersection work in the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--create-steps", type=int, default=3,
+                   help="timed tc_graph_create calls from device-resident edges")
+    p.add_argument("--no-extra", action="store_true",
+                   help="R-MAT 24 headline only: skip the mesh, batched and serving keys")
+    p.add_argument("--serve-requests-extra", type=int, default=1000,
+                   help="requests per arrival-rate point of the serving key in the default line")
+    p.add_argument("--cpu-validate", action="store_true",
+                   help="time the full OpenMP oracle count and compare it with the sampled "
+                        "estimate (CPU only)")
     return p.parse_args()
 
 
@@ -238,15 +247,18 @@ def kernel_source_sha() -> str:
 
 
 def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the owner-hash kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    """DRAM bytes per launch of the owner-hash kernel from the committed ncu summary.
+
+    Returns (bytes or None, stale): stale is True when a summary exists but was taken on
+    another revision of the kernel source, so its bytes no longer describe this kernel.
+    """
     path = os.path.join(ROOT, "profiles", f"owner_hash_{workload}.json")
     if not os.path.exists(path):
-        return None
+        return None, False
     d = json.load(open(path))
     if d.get("source_sha") != kernel_source_sha():
-        return None
-    return d.get("dram_bytes_per_launch")
+        return None, True
+    return d.get("dram_bytes_per_launch"), False
 
 
 # ----------------------------------------------------------------------------
@@ -254,72 +266,105 @@ def profiled_traffic(workload: str):
 # ----------------------------------------------------------------------------
 
 class OracleSampler:
-    """Times the oracle (as it stands) on a bounded sample of the workload.
+    """Times the oracle, as it stands, on a bounded sample of the workload.
 
     The graph is built by the oracle (not timed, as tc_graph_create is not in
-    the GPU step).  A sample = the oracle BFS over the whole graph, its full
-    cover-edge scan, and the literal CETC-Seq intersection of a seeded uniform
-    random sample of the cover edges, grown geometrically until it has used
-    about target_s seconds.  The full-graph time is estimated as
-    bfs + scan + (sample wall time / sampled edges) * |S|.
+    the GPU step).  One sample (`step`) times, on this host:
 
-    The sampled intersections run on `cores` host threads, as Algorithm
-    CETC-SM spreads the cover-edge loop: each thread calls the oracle's edge
-    loop on a slice of the sample (ctypes releases the GIL during the call).
-    BFS and scan stay single-threaded, as the oracle has them.
+    * the oracle BFS over the whole graph with its restarts (one thread);
+    * its cover-edge scan: the CETC-Seq edge loop with the intersections
+      sampled out (orc_cetc with a stride beyond |S|; one thread);
+    * the per-edge intersections of a seeded uniform sample of S, twice:
+      ``seq``, the literal CETC-Seq edge loop on one thread (orc_cetc_edges),
+      and ``omp``, Algorithm CETC-SM's parallel edge loop on all host threads
+      (orc_cetc_sm_edges).  Each sample grows geometrically until it has used
+      about its time budget.
+
+    The full-graph time of each baseline is estimated as
+    bfs + scan + (sample seconds / sampled edges) x |S|; `wall` is what the
+    sample itself took.  Counts of the sampled edges are not used (the GPU arm
+    checks its count against the oracle elsewhere).
     """
 
-    def __init__(self, spec, src, dst, root, target_s, seed=11, cores=None):
+    def __init__(self, spec, src, dst, root, target_s, seed=11):
         import oracle
         self.o = oracle
         self.rp, self.col = oracle.build_csr(spec.n, src, dst)
         self.m = int(self.col.size // 2)
         self.root = root
-        self.target_s = max(float(target_s), 0.5)
+        self.target_s = max(float(target_s), 0.2)
         self.rng = np.random.default_rng(seed)
-        self.cores = max(1, int(cores or os.cpu_count() or 1))
+        self.cores = int(oracle.num_threads())
+        self.num_cover = None
 
-    def _edges(self, lv, us, vs) -> int:
-        """The oracle's count over the given cover edges, on self.cores threads."""
-        if self.cores == 1 or us.size < 4 * self.cores:
-            return self.o.cetc_edges(self.rp, self.col, lv, us, vs)["T"]
-        from concurrent.futures import ThreadPoolExecutor
-        parts = np.array_split(np.arange(us.size), self.cores)
-        with ThreadPoolExecutor(self.cores) as ex:
-            return sum(r["T"] for r in ex.map(
-                lambda ix: self.o.cetc_edges(self.rp, self.col, lv, us[ix], vs[ix]), parts))
-
-    def step(self) -> dict:
-        t = time.perf_counter()
-        lv = self.o.bfs_levels(self.rp, self.col, self.root)
-        t_bfs = time.perf_counter() - t
-        t = time.perf_counter()
-        cov = self.o.cetc(self.rp, self.col, lv, stride=1 << 62, want_cover=True)
-        t_scan = time.perf_counter() - t
-        S = cov["num_cover"]
-        done, t_sample, k = 0, 0.0, 256
-        while S and t_sample < self.target_s and done < S:
+    def _sample(self, fn, lv, cov, budget):
+        """Grows a uniform sample of S until about `budget` seconds; (edges, seconds)."""
+        S = self.num_cover
+        done, spent, k = 0, 0.0, 64
+        while S and spent < budget and done < 4 * S:
             k = min(k, S)
             idx = self.rng.integers(0, S, size=k)
             us, vs = cov["cover_u"][idx], cov["cover_v"][idx]
             t = time.perf_counter()
-            self._edges(lv, us, vs)
+            fn(self.rp, self.col, lv, us, vs)
             dt = time.perf_counter() - t
-            t_sample += dt
+            spent += dt
             done += k
-            # grow toward the remaining budget, at most 4x per round
-            k = int(k * min(4.0, max(1.5, (self.target_s - t_sample) / max(dt, 1e-6))))
-        per_edge = t_sample / done if done else 0.0
-        est = t_bfs + t_scan + per_edge * S
-        self.done, self.num_cover = done, S
-        return {"est_seconds": est, "edges": self.m, "done": done,
-                "wall": t_bfs + t_scan + t_sample}
+            k = int(k * min(4.0, max(1.5, (budget - spent) / max(dt, 1e-6))))
+        return done, spent
 
-    def describe(self, done) -> str:
-        return (f"oracle BFS over the whole graph + full cover-edge scan + literal CETC-Seq "
-                f"intersection of {done} uniformly sampled cover edges of {self.num_cover}; "
-                f"full-graph time = bfs + scan + per-edge sample wall time x |S|; "
-                f"intersections on {self.cores} host threads")
+    def step(self) -> dict:
+        t0 = time.perf_counter()
+        lv = self.o.bfs_levels(self.rp, self.col, self.root)
+        t_bfs = time.perf_counter() - t0
+        t = time.perf_counter()
+        cov = self.o.cetc(self.rp, self.col, lv, stride=1 << 62, want_cover=True)
+        t_scan = time.perf_counter() - t
+        self.num_cover = S = cov["num_cover"]
+        out = {"edges": self.m, "num_cover": S, "bfs_s": t_bfs, "scan_s": t_scan}
+        for name, fn, share in (("seq", self.o.cetc_edges, 0.4), ("omp", self.o.cetc_sm_edges, 0.6)):
+            done, spent = self._sample(fn, lv, cov, share * self.target_s)
+            est = t_bfs + t_scan + (spent / done) * S if done else t_bfs + t_scan
+            out[name] = {"sampled_edges": done, "sample_s": spent, "est_full_seconds": est,
+                         "cores": 1 if name == "seq" else self.cores,
+                         "value": self.m / est if est > 0 else None}
+        out["wall"] = time.perf_counter() - t0
+        return out
+
+    def describe(self, r) -> str:
+        return (f"oracle BFS over the whole graph + full cover-edge scan (1 thread each), then the "
+                f"per-edge intersections of seeded uniform samples of S (|S| = {r['num_cover']}): "
+                f"{r['seq']['sampled_edges']} edges by the literal CETC-Seq loop on 1 thread, "
+                f"{r['omp']['sampled_edges']} by the CETC-SM parallel loop on {self.cores} "
+                f"threads; full-graph time = bfs + scan + sample seconds per edge x |S|")
+
+    def baseline(self, r) -> dict:
+        """The cpu_baseline object: the OpenMP form (all cores) with the one-thread form beside."""
+        return {"value": r["omp"]["value"], "unit": "edges/s", "cores": self.cores,
+                "kind": "oracle", "sample": self.describe(r),
+                "est_full_seconds": r["omp"]["est_full_seconds"], "sample_wall_s": r["wall"],
+                "seq": r["seq"], "omp": r["omp"]}
+
+
+def validate_cpu_estimate(spec, src, dst, root, target_s):
+    """The sampled full-graph estimate against a full timed run of the same loop.
+
+    Times the OpenMP edge loop (orc_cetc_sm_edges) over all of S once and compares it with the
+    sampler's estimate of the same (both after the same BFS and scan).
+    """
+    import oracle
+    sam = OracleSampler(spec, src, dst, root, target_s)
+    r = sam.step()
+    lv = oracle.bfs_levels(sam.rp, sam.col, root)
+    cov = oracle.cetc(sam.rp, sam.col, lv, stride=1 << 62, want_cover=True)
+    t = time.perf_counter()
+    full = oracle.cetc_sm_edges(sam.rp, sam.col, lv, cov["cover_u"], cov["cover_v"])
+    t_full = time.perf_counter() - t + r["bfs_s"] + r["scan_s"]
+    est = r["omp"]["est_full_seconds"]
+    return {"workload": spec.family, "n": spec.n, "m": sam.m, "num_cover": r["num_cover"],
+            "cores": sam.cores, "triangles": full["T"], "full_seconds": t_full,
+            "estimated_seconds": est, "relative_error": (est - t_full) / t_full,
+            "sampled_edges": r["omp"]["sampled_edges"], "sample_seconds": r["omp"]["sample_s"]}
 
 
 # ----------------------------------------------------------------------------
@@ -327,6 +372,13 @@ class OracleSampler:
 # ----------------------------------------------------------------------------
 
 def run_reference(args, world, rank):
+    """The oracle as it stands on this host's cores (the reference arm).
+
+    Each step is one bounded sample (OracleSampler.step); ms_per_step is its
+    measured wall time.  value = input edges / the estimated full-graph time of
+    Algorithm CETC-SM's parallel loop on all host threads (median over steps),
+    the same figure as the GPU arm's cpu_baseline.
+    """
     if rank != 0:
         return 0
     spec = WORKLOADS[args.workload]
@@ -335,24 +387,27 @@ def run_reference(args, world, rank):
     rp, _ = oracle.build_csr(spec.n, src, dst)
     root = oracle.max_degree_root(rp) if spec.root == "maxdeg" else 0
     del rp
-    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    budget = max(2.0, 90.0 / max(1, args.steps + args.warmup))
     sam = OracleSampler(spec, src, dst, root, target_s=budget)
     for _ in range(args.warmup):
         sam.step()
-    tot_edges, tot_s, done = 0, 0.0, 0
+    walls, ests, last = [], [], None
     for _ in range(args.steps):
-        r = sam.step()
-        tot_edges += r["edges"]
-        tot_s += r["est_seconds"]
-        done = r["done"]
-    value = tot_edges / tot_s
+        last = sam.step()
+        walls.append(last["wall"])
+        ests.append(last["omp"]["est_full_seconds"])
+    est = statistics.median(ests)
+    value = sam.m / est
+    base = dict(sam.baseline(last), value=value, est_full_seconds=est)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
+            "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": config_dict(spec, args),
-            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": sam.cores, "kind": "oracle",
-                             "sample": sam.describe(done)},
+            "timing": ("ms_per_step: measured wall time of one bounded sample; value: input edges "
+                       "/ the estimated full-graph time of the CETC-SM oracle on all host threads"),
+            "est_full_seconds": est,
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -391,6 +446,16 @@ def run_ours(args, world, rank, local):
         d_src = h_src.to("cuda", non_blocking=True)
         d_dst = h_dst.to("cuda", non_blocking=True)
     stream.synchronize()
+    # tc_graph_create from device-resident edges (radix-sort CSR build, allocation included),
+    # host wall time with the device idle on both sides
+    create_s = []
+    for _ in range(args.create_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gc = tc.Graph(d_src, d_dst, spec.n, stream=stream)
+        stream.synchronize()
+        create_s.append(time.perf_counter() - t0)
+        gc.close()
     g = tc.Graph(d_src, d_dst, spec.n, stream=stream)
     del d_src, d_dst
     root = g.max_degree_vertex() if spec.root == "maxdeg" else 0
@@ -461,7 +526,8 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
     achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0
-    traffic = profiled_traffic(args.workload)
+    traffic, traffic_stale = profiled_traffic(args.workload)
+    dram_rate = traffic / (hash_ms / 1e3) / 1e9 if traffic and hash_ms > 0 else None
 
     # end to end through the C ABI from pinned host buffers
     e2e_steps = args.e2e_steps
@@ -485,17 +551,11 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             sam = OracleSampler(spec, src, dst, root, target_s=args.cpu_seconds)
-            r = sam.step()
-            cpu = {"value": r["edges"] / r["est_seconds"], "unit": "edges/s", "cores": sam.cores,
-                   "kind": "oracle", "sample": sam.describe(r["done"]),
-                   "est_full_seconds": r["est_seconds"]}
+            cpu = sam.baseline(sam.step())
         except Exception as e:  # keep the GPU line even if the host runs short
             cpu = {"value": None, "unit": "edges/s", "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e}"}
 
-    if rank != 0:
-        g.close()
-        return 0
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
@@ -512,11 +572,19 @@ def run_ours(args, world, rank, local):
                 "bottom_up_steps": st["bottom_up_steps"], "restarted": st["restarted"]},
         "roofline": {"bound": "hbm", "kernel": "k_owner_hash", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
-                     "peak_kind": peak_kind, "traffic": traffic,
+                     "peak_kind": peak_kind, "traffic": traffic, "traffic_stale": traffic_stale,
+                     "frac_alg": achieved / peak if peak else None,
+                     "frac_dram": dram_rate / peak if dram_rate and peak else None,
+                     "achieved_dram": dram_rate,
                      "alg_bytes_per_launch": hb["bytes"], "hash_edges": hb["edges"],
                      "hash_items": hb["items"], "streamed_elements": hb["streamed_elements"],
                      "streamer_row_elements": hb["row_elements"],
                      "survey_alg_bytes_per_count": survey_bytes},
+        "create": {"seconds": statistics.median(create_s) if create_s else None,
+                   "input_edges_per_s": E / statistics.median(create_s) if create_s else None,
+                   "input_bytes_per_s": 8 * E / statistics.median(create_s) if create_s else None,
+                   "what": "tc_graph_create from device-resident edge lists: key build, radix "
+                           "sort, dedup, CSR (allocation included)"},
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 8 * E,
                 "d2h_bytes_per_step": 8, "seconds_per_step": e2e_max},
         "gpu_launches": launches,
@@ -524,12 +592,69 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "variants": variants,
     }
-    print(json.dumps(line), flush=True)
     g.close()
+    del g
+    torch.cuda.synchronize()
+    if args.workload == "rmat24" and not args.no_extra:
+        # the other workloads of the same campaign, each with its own clock record
+        line["mesh4096"] = measure_mesh(args, world, rank, local)
+        line["batched"] = measure_batched(args, world, rank, local)
+        line["serve"] = measure_serve(args, world, rank, local, requests=args.serve_requests_extra,
+                                      loads=(0.1, 0.6, 0.9))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args, world, rank, local):
+def measure_mesh(args, world, rank, local) -> dict:
+    """tc_count on the 4096 x 4096 random-diagonal mesh (about 8191 BFS levels).
+
+    Its count must equal the closed form 2 D (D = diagonals present): each
+    anti-diagonal lies in exactly two triangles and the 4-neighbour grid has none.
+    """
+    import torch
+    import paper_2403_02997_gb300 as tc
+    from paper_2403_02997_gb300 import autotune
+    spec = replica_spec(gen.MESH_4096, rank)
+    src, dst = spec.edges()
+    diagonals = int(gen.mesh_diagonals(spec.rows, spec.cols, spec.p, spec.seed).sum())
+    stream = torch.cuda.Stream()
+    d_src = torch.from_numpy(src.view(np.int32)).cuda()
+    d_dst = torch.from_numpy(dst.view(np.int32)).cuda()
+    g = tc.Graph(d_src, d_dst, spec.n, stream=stream)
+    del d_src, d_dst
+    tuned = None if args.no_tuned else autotune.lookup(
+        autotune.signature(spec.n, g.m, g.d_max, spec.family))
+    if tuned:
+        g.set_params(**tuned)
+    for _ in range(max(args.warmup, 3)):
+        T = g.count(0, stream=stream)
+    steps = max(args.steps, 5)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        assert g.count(0, stream=stream) == T
+    ev1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    st = g.stats()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, world)
+    m = g.m
+    g.close()
+    return {"workload": "mesh 4096 x 4096, 4-neighbour + anti-diagonals p=0.5 (seed 7), root 0",
+            "ms_per_count": ms, "edges_per_s": sum_over_ranks(float(m), world) / (ms / 1e3),
+            "m": m, "triangles": T, "closed_form_2D": 2 * diagonals,
+            "closed_form_ok": T == 2 * diagonals, "levels": st["num_levels"],
+            "phase_ms": {"bfs": st["ms_bfs"], "cover": st["ms_cover"],
+                         "intersect": st["ms_intersect"]},
+            "steps": steps, "params": tuned or "defaults", "clocks": clk}
+
+
+def measure_batched(args, world, rank, local) -> dict:
     """The batched workload: graphs of uneven size counted together.
 
     value = graphs counted per second by tc_batch_count on device-resident
@@ -606,15 +731,10 @@ def run_batched(args, world, rank, local):
     assert many_counts == counts
     for g in gs:
         g.close()
-    if rank != 0:
-        return 0
     h2d = sum(8 * int(s.size) for s, _ in edges)
-    line = {
+    return {
         "metric": f"graphs/s (batched count of {len(gs)} graphs, device-resident)",
-        "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded counter-based generator)",
+        "graphs_per_s": value, "ms_per_batch": ms / args.steps, "steps": args.steps,
         "config": {"workload": "batched", "graphs": len(gs), "n_log_uniform": [64, 65536],
                    "families": "even: ER mean degree U[4,64]; odd: R-MAT ef U{8..16}",
                    "master_seed": 4, "vertices": int(sum(sp.n for sp in specs)),
@@ -633,25 +753,39 @@ def run_batched(args, world, rank, local):
         "e2e_per_graph_handles": {"graphs_per_s": len(gs) / t_many, "seconds": t_many,
                                   "what": "tc_graph_create per graph + tc_count_many"},
         "gpu_launches": st["launches"] * args.steps,
+        "launches_per_batch": st["launches"],
         "clocks": clk,
     }
+
+
+def run_batched(args, world, rank, local):
+    """The batched workload as its own JSON line (graphs/s)."""
+    r = measure_batched(args, world, rank, local)
+    if rank != 0:
+        return 0
+    line = {"metric": r["metric"], "value": r["graphs_per_s"], "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded counter-based generator)"}
+    line.update({k: v for k, v in r.items() if k not in ("metric", "graphs_per_s")})
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args, world, rank, local):
+def measure_serve(args, world, rank, local, requests=None, loads=(0.1, 0.3, 0.6, 0.9, 1.2)) -> dict:
     """The serving workload: Poisson arrivals of count requests.
 
     Requests are drawn from the batched distribution, a pool of 512 graphs with n log-uniform on
     [2^6, 2^16], seed 5. Every 100th request is an R-MAT scale-22, edge-factor-16 graph, which is
     the 1 %. The capacity is first measured with every request arriving at once. The sweep then
-    runs at 0.1, 0.3, 0.6, 0.9 and 1.2 times that capacity and reports graphs/s and p50/p99
-    latency from arrival to count.
+    runs at the given fractions of that capacity and reports graphs/s and p50/p99 latency from
+    arrival to count, and how much of the device time the batch builds overlapped with counts.
     """
     import torch
-    from paper_2403_02997_gb300 import autotune, build as tcbuild, serve
-    tcbuild.build_all()
+    from paper_2403_02997_gb300 import autotune, serve
     torch.cuda.set_device(local)
+    requests = requests or args.serve_requests
     specs = gen.batched_specs(512, master_seed=5 + 1000 * rank)
     pool = [(*sp.edges(), sp.n, None if sp.root == "maxdeg" else 0) for sp in specs]
     big = [(*gen.rmat_spec(22, 16, 22 + i + 1000 * rank).edges(), 1 << 22, None) for i in range(2)]
@@ -659,35 +793,51 @@ def run_serve(args, world, rank, local):
     budget = int(args.serve_budget_gb * (1 << 30))
     srv = serve.Server(hbm_budget_bytes=budget, params=tuned)
     serve.run_arrivals(srv, pool, rate=1e6, count=200, seed=1)          # warm-up
-    sat = serve.run_arrivals(srv, pool, rate=1e9, count=args.serve_requests, seed=2,
+    clocks = ClockSampler(local)
+    clocks.start()
+    sat = serve.run_arrivals(srv, pool, rate=1e9, count=requests, seed=2,
                              big_every=100, big_pool=big)
+    sat.pop("requests_list")
     capacity = sat["graphs_per_s"]
     points = []
-    for f in (0.1, 0.3, 0.6, 0.9, 1.2):
-        r = serve.run_arrivals(srv, pool, rate=f * capacity, count=args.serve_requests,
+    for f in loads:
+        r = serve.run_arrivals(srv, pool, rate=f * capacity, count=requests,
                                seed=int(100 * f), big_every=100, big_pool=big)
         r.pop("requests_list")
         r["load"] = f
         points.append(r)
+    clk = clocks.stop()
     batches = list(srv.batches)
+    overlap = srv.overlap_stats()
     srv.close()
-    if rank != 0:
-        return 0
     knee = next((p["load"] for p in points if p["p99_ms"] and points[0]["p99_ms"] and
                  p["p99_ms"] > 5 * points[0]["p99_ms"]), None)
-    line = {
+    return {
         "metric": "served graphs/s and p50/p99 latency (continuous batching, Poisson arrivals)",
-        "value": max(p["graphs_per_s"] for p in points), "unit": "graphs/s", "n_gpus": world,
-        "steps": len(points), "warmup": 1, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
+        "graphs_per_s": max(p["graphs_per_s"] for p in points),
         "config": {"workload": "serve", "pool": "512 graphs, n log-uniform [2^6, 2^16] (seed 5)",
-                   "big": "1 % R-MAT scale 22 ef 16", "requests_per_point": args.serve_requests,
+                   "big": "1 % R-MAT scale 22 ef 16", "requests_per_point": requests,
                    "hbm_budget_gb": args.serve_budget_gb, "params": tuned or "defaults"},
-        "capacity_graphs_per_s": capacity, "saturated_p50_ms": sat["p50_ms"],
-        "saturated_p99_ms": sat["p99_ms"], "sweep": points, "p99_knee_load": knee,
+        "capacity_graphs_per_s": capacity, "saturated": sat, "sweep": points,
+        "p99_knee_load": knee,
         "mean_batch": float(np.mean(batches)) if batches else None,
         "max_batch": int(max(batches)) if batches else None,
+        "overlap": overlap, "clocks": clk,
     }
+
+
+def run_serve(args, world, rank, local):
+    """The serving workload as its own JSON line (peak served graphs/s over the sweep)."""
+    from paper_2403_02997_gb300 import build as tcbuild
+    tcbuild.build_all()
+    r = measure_serve(args, world, rank, local)
+    if rank != 0:
+        return 0
+    line = {"metric": r["metric"], "value": r["graphs_per_s"], "unit": "graphs/s",
+            "n_gpus": world, "steps": len(r["sweep"]), "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded counter-based generator)"}
+    line.update({k: v for k, v in r.items() if k not in ("metric", "graphs_per_s")})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -696,6 +846,15 @@ def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     try:
+        if args.cpu_validate:
+            spec = WORKLOADS[args.workload]
+            src, dst = spec.edges()
+            import oracle
+            rp, _ = oracle.build_csr(spec.n, src, dst)
+            root = oracle.max_degree_root(rp) if spec.root == "maxdeg" else 0
+            del rp
+            print(json.dumps(validate_cpu_estimate(spec, src, dst, root, args.cpu_seconds)))
+            return 0
         if args.impl == "reference":
             if args.workload in ("batched", "serve"):
                 print(json.dumps({"impl": "reference", "unavailable":

@@ -85,7 +85,12 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
 tc_status tc_graph_relabel_degree(const tc_graph* g, void* stream, tc_graph** out,
                                   uint32_t* host_old_of_new);
 
-/* Free the handle and all device memory it owns.  NULL is accepted. */
+/*
+ * Free the handle and all device memory it owns.  NULL is accepted.  Every
+ * call on a handle has finished its device work when it returns (each
+ * synchronises its own stream), so destroy adds no synchronisation of its own
+ * (cudaFree itself waits for the device).
+ */
 tc_status tc_graph_destroy(tc_graph* g);
 
 /*
@@ -275,6 +280,15 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
  * rows sorted), exactly as tc_graph_create does per graph.  Errors as
  * tc_batch_create, plus TC_ERR_VERTEX_RANGE when an id is >= its own graph's
  * vertex count.
+ *
+ * Memory: everything this batch uses on the device, the build's sort buffers
+ * included, is taken in stream order on `stream` from the library's memory
+ * pool for the current device, and tc_batch_destroy returns it in stream
+ * order on a library-owned stream.  So building one batch and destroying
+ * another never synchronises the device (a serving loop builds on one stream
+ * while it counts on another).  The pool keeps freed memory reserved for the
+ * next build; tc_pool_trim returns it to the driver.  Pass pinned host arrays
+ * for the copies to run asynchronously.
  */
 tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
                                      const uint64_t* edge_offsets, const uint32_t* num_vertices,
@@ -288,7 +302,19 @@ tc_status tc_batch_set_params(tc_batch* b, const tc_params* p);
 tc_status tc_batch_get_stats(const tc_batch* b, tc_stats* out);
 /* Levels of graph i after tc_batch_count: host_levels[n_i]. */
 tc_status tc_batch_get_levels(const tc_batch* b, size_t i, int32_t* host_levels);
+/* Free a batch (NULL is accepted); no device-wide synchronisation for batches
+ * from tc_batch_create_from_edges (see there). */
 tc_status tc_batch_destroy(tc_batch* b);
+
+/*
+ * The library's memory pool on the current device (stream-ordered memory of
+ * the batches built from edge lists).  tc_pool_trim releases reserved but
+ * unused memory until at most keep_bytes stay reserved (it synchronises the
+ * library's free stream first); tc_pool_reserved reports the bytes the pool
+ * holds from the driver now.  Errors: TC_ERR_INVALID_ARG (NULL), TC_ERR_CUDA.
+ */
+tc_status tc_pool_trim(uint64_t keep_bytes);
+tc_status tc_pool_reserved(uint64_t* bytes);
 
 /*
  * BFS levels of a caller-owned device graph, allocating no device memory.
@@ -301,8 +327,8 @@ tc_status tc_batch_destroy(tc_batch* b);
  * are an undirected graph in CSR form: every edge in both rows, no self-loops;
  * rows need not be sorted (tc_get_csr's output qualifies).  levels (device, n
  * int32) receives L(v): the BFS distance from root, and for vertices the root
- * does not reach, the distance from the smallest id of their component (the
- * restart rule of Algorithm CETC-Seq), so every entry ends >= 0.  The caller
+ * does not reach, the distance from the smallest id of their connected
+ * component, so every entry ends >= 0.  The caller
  * owns all three arrays; nothing is retained after the call returns.  Work is
  * ordered on `stream`, which the call synchronises once per BFS level.
  *

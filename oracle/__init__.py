@@ -60,6 +60,9 @@ def _load():
         lib.orc_num_threads.argtypes = []
         lib.orc_cetc_edges.restype = None
         lib.orc_cetc_edges.argtypes = [_i64p, _u32p, _i32p, ctypes.c_uint64, _u32p, _u32p, _u64p]
+        lib.orc_cetc_sm_edges.restype = None
+        lib.orc_cetc_sm_edges.argtypes = [_i64p, _u32p, _i32p, ctypes.c_uint64, _u32p, _u32p,
+                                          _u64p]
         lib.orc_edge_count.restype = ctypes.c_uint64
         lib.orc_edge_count.argtypes = [_i64p, _u32p, _i32p, ctypes.c_uint32, ctypes.c_uint32]
         lib.orc_triples.restype = ctypes.c_uint64
@@ -142,6 +145,16 @@ def cetc_edges(row_ptr, col, level, us, vs) -> dict:
     out = np.zeros(3, dtype=np.uint64)
     _load().orc_cetc_edges(_p(row_ptr, _i64p), _p(col, _u32p), _p(level, _i32p), us.size,
                            _p(us, _u32p), _p(vs, _u32p), _p(out, _u64p))
+    return dict(T=int(out[0]), c1=int(out[1]), c2=int(out[2]))
+
+
+def cetc_sm_edges(row_ptr, col, level, us, vs) -> dict:
+    """cetc_edges with the edge loop spread over all host threads (Algorithm CETC-SM)."""
+    us = np.ascontiguousarray(us, dtype=np.uint32)
+    vs = np.ascontiguousarray(vs, dtype=np.uint32)
+    out = np.zeros(3, dtype=np.uint64)
+    _load().orc_cetc_sm_edges(_p(row_ptr, _i64p), _p(col, _u32p), _p(level, _i32p), us.size,
+                              _p(us, _u32p), _p(vs, _u32p), _p(out, _u64p))
     return dict(T=int(out[0]), c1=int(out[1]), c2=int(out[2]))
 
 

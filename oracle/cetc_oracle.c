@@ -252,6 +252,27 @@ void orc_cetc_edges(const int64_t* row_ptr, const uint32_t* col, const int32_t* 
 }
 
 /*
+ * orc_cetc_edges run as Algorithm CETC-SM runs its cover-edge loop: the k
+ * given horizontal edges split over the host's OpenMP threads (dynamic
+ * schedule), per-edge counts summed.  Same outputs as orc_cetc_edges; used to
+ * time a sample of the parallel edge loop on all host cores.
+ */
+void orc_cetc_sm_edges(const int64_t* row_ptr, const uint32_t* col, const int32_t* level,
+                       uint64_t k, const uint32_t* us, const uint32_t* vs, uint64_t* out) {
+  uint64_t t = 0, c1 = 0, c2 = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : t, c1, c2)
+  for (int64_t i = 0; i < (int64_t)k; ++i) {
+    uint64_t a = 0, b = 0;
+    t += cover_edge(row_ptr, col, level, us[i], vs[i], &a, &b);
+    c1 += a;
+    c2 += b;
+  }
+  out[0] = t;
+  out[1] = c1;
+  out[2] = c2;
+}
+
+/*
  * The per-edge count of Algorithm CETC-Seq for one horizontal edge (u, v),
  * u < v: the number of w in N(u) ∩ N(v) with L(u) != L(w), or L(u) == L(w)
  * and v < w.

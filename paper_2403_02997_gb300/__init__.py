@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
         "tc_batch_get_stats": ([vp, P(tc_stats)], ctypes.c_int),
         "tc_batch_get_levels": ([vp, ctypes.c_size_t, vp], ctypes.c_int),
         "tc_batch_destroy": ([vp], ctypes.c_int),
+        "tc_pool_trim": ([u64], ctypes.c_int),
+        "tc_pool_reserved": ([P(u64)], ctypes.c_int),
         "tc_batch_create_from_edges": ([vp, vp, P(u64), P(u32), ctypes.c_size_t, ctypes.c_int,
                                         vp, P(vp)], ctypes.c_int),
         "tc_batch_max_degree_vertices": ([vp, vp, P(u32)], ctypes.c_int),
@@ -374,6 +376,39 @@ def count_many(graphs: Sequence[Graph], roots: Sequence[int], stream=None) -> li
     return tc_count_many([g.handle for g in graphs], roots, stream)
 
 
+class PinnedStaging:
+    """Reusable page-locked host buffers for batch builds from edge lists.
+
+    tc_batch_create_from_edges copies the edges to the device and has finished
+    with them when it returns, so the same buffers serve the next build.
+    """
+
+    def __init__(self):
+        self.buf = None
+
+    def arrays(self, count: int):
+        """Two uint32 arrays of `count` entries (src, dst) in pinned memory."""
+        need = 2 * int(count)
+        if self.buf is None or self.buf.numel() < need:
+            import torch
+            size = max(need, 1 << 20, int(1.5 * (self.buf.numel() if self.buf is not None else 0)))
+            self.buf = torch.empty(size, dtype=torch.int32, pin_memory=True)
+        a = self.buf.numpy().view(np.uint32)
+        return a[:count], a[count:2 * count]
+
+
+def pool_trim(keep_bytes: int = 0) -> None:
+    """Return the library pool's unused device memory to the driver (keep at most keep_bytes)."""
+    _check(load_library().tc_pool_trim(int(keep_bytes)), "tc_pool_trim")
+
+
+def pool_reserved() -> int:
+    """Device bytes the library's pool holds now."""
+    v = ctypes.c_uint64()
+    _check(load_library().tc_pool_reserved(ctypes.byref(v)), "tc_pool_reserved")
+    return int(v.value)
+
+
 class Batch:
     """A reusable batch: the graphs' CSRs concatenated once, counted together."""
 
@@ -388,8 +423,12 @@ class Batch:
         self.handle = out.value
 
     @classmethod
-    def from_edges(cls, graphs, stream=None) -> "Batch":
-        """Build a batch straight from host edge lists: graphs = [(src, dst, n), ...]."""
+    def from_edges(cls, graphs, stream=None, staging: Optional["PinnedStaging"] = None) -> "Batch":
+        """Build a batch straight from host edge lists: graphs = [(src, dst, n), ...].
+
+        With `staging`, the edge lists are gathered into its page-locked buffers, so the
+        library's host-to-device copies run asynchronously on `stream`.
+        """
         lib = load_library()
         self = cls.__new__(cls)
         self.k = len(graphs)
@@ -397,10 +436,16 @@ class Batch:
         lens = [int(np.asarray(s_).size) for s_, _, _ in graphs]
         offs = np.zeros(self.k + 1, dtype=np.uint64)
         offs[1:] = np.cumsum(lens, dtype=np.uint64)
-        src = np.concatenate([np.asarray(s_, np.uint32) for s_, _, _ in graphs]) if lens else \
-            np.zeros(0, np.uint32)
-        dst = np.concatenate([np.asarray(d_, np.uint32) for _, d_, _ in graphs]) if lens else \
-            np.zeros(0, np.uint32)
+        total = int(offs[-1])
+        if staging is not None and total:
+            src, dst = staging.arrays(total)
+            np.concatenate([np.asarray(s_, np.uint32) for s_, _, _ in graphs], out=src)
+            np.concatenate([np.asarray(d_, np.uint32) for _, d_, _ in graphs], out=dst)
+        else:
+            src = np.concatenate([np.asarray(s_, np.uint32) for s_, _, _ in graphs]) if lens \
+                else np.zeros(0, np.uint32)
+            dst = np.concatenate([np.asarray(d_, np.uint32) for _, d_, _ in graphs]) if lens \
+                else np.zeros(0, np.uint32)
         nv = np.asarray(self.sizes, dtype=np.uint32)
         out = ctypes.c_void_p()
         _check(lib.tc_batch_create_from_edges(

@@ -110,12 +110,20 @@ __global__ void __launch_bounds__(kGatherBlock) k_batch_maxdeg(
   }
 }
 
-// Counters, pinned mirror and events of a union handle.
-tc_status init_union(tc_graph* u) {
+// Counters, host mirror and events of a union handle (a pooled handle's
+// mirror is pageable: freeing pinned memory would synchronise the device).
+tc_status init_union(tc_graph* u, cudaStream_t st) {
   params_default(&u->params);
   std::memset(&u->stats, 0, sizeof(u->stats));
-  if (cudaMalloc(&u->ctr, sizeof(DevCounters)) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&u->ctr_host), sizeof(DevCounters)) != cudaSuccess) {
+  if (dev_alloc(u, &u->ctr, 1, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_OOM;
+  }
+  if (u->pooled) {
+    u->ctr_host = new (std::nothrow) DevCounters();
+    if (!u->ctr_host) return TC_ERR_OOM;
+  } else if (cudaMallocHost(reinterpret_cast<void**>(&u->ctr_host), sizeof(DevCounters)) !=
+             cudaSuccess) {
     cudaGetLastError();
     return TC_ERR_OOM;
   }
@@ -125,17 +133,22 @@ tc_status init_union(tc_graph* u) {
   return TC_OK;
 }
 
+// Frees a batch.  Every call on it finished its work before returning, so a
+// pooled batch's memory goes back on the library's stream, with no
+// device-wide synchronisation.
 void free_batch(tc_batch* b) {
   if (!b) return;
-  if (b->u) {
-    b->u->voff = nullptr;
-    b->u->gcount = nullptr;
-    free_graph(b->u);
+  tc_graph* u = b->u;
+  cudaStream_t fs = u && u->pooled ? free_stream() : nullptr;
+  dev_free(u, b->voff, fs);
+  dev_free(u, b->eoff, fs);
+  dev_free(u, b->gcount, fs);
+  dev_free(u, b->roots, fs);
+  if (u) {
+    u->voff = nullptr;
+    u->gcount = nullptr;
+    free_graph(u);
   }
-  cudaFree(b->voff);
-  cudaFree(b->eoff);
-  cudaFree(b->gcount);
-  cudaFree(b->roots);
   delete b;
 }
 
@@ -181,7 +194,7 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
     tc_graph* u = new (std::nothrow) tc_graph();
     if (!u) { s = TC_ERR_OOM; break; }
     b->u = u;
-    if ((s = init_union(u)) != TC_OK) break;
+    if ((s = init_union(u, st)) != TC_OK) break;
     u->n = (uint32_t)voff[k];
     u->nnz = eoff[k];
     u->m = u->nnz / 2;
@@ -214,7 +227,7 @@ tc_status tc_batch_create(tc_graph* const* gs, size_t k, void* stream, tc_batch*
       k_gather_cols<<<grid_for(u->nnz, kGatherTile, sms * 16), kGatherBlock, 0, st>>>(
           d_parts, b->voff, b->eoff, b->k, u->nnz, u->col);
     if (cudaGetLastError() != cudaSuccess) { s = TC_ERR_CUDA; break; }
-    if ((s = alloc_count_state(u)) != TC_OK) break;
+    if ((s = alloc_count_state(u, st)) != TC_OK) break;
     u->batch_k = b->k;
     u->voff = b->voff;
     u->gcount = b->gcount;
@@ -259,13 +272,14 @@ tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
     tc_graph* u = new (std::nothrow) tc_graph();
     if (!u) { s = TC_ERR_OOM; break; }
     b->u = u;
-    if ((s = init_union(u)) != TC_OK) break;
+    u->pooled = true;  // built and freed while other batches count (serving)
+    if ((s = init_union(u, st)) != TC_OK) break;
     u->n = (uint32_t)voff[k];
-    if (cudaMalloc(&b->voff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
-        cudaMalloc(&b->eoff, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
-        cudaMalloc(&b->gcount, sizeof(unsigned long long) * k) != cudaSuccess ||
-        cudaMalloc(&b->roots, sizeof(uint32_t) * k) != cudaSuccess ||
-        cudaMalloc(&d_nvert, sizeof(uint32_t) * k) != cudaSuccess) {
+    if (dev_alloc(u, &b->voff, k + 1, st) != cudaSuccess ||
+        dev_alloc(u, &b->eoff, k + 1, st) != cudaSuccess ||
+        dev_alloc(u, &b->gcount, k, st) != cudaSuccess ||
+        dev_alloc(u, &b->roots, k, st) != cudaSuccess ||
+        dev_alloc(u, &d_nvert, k, st) != cudaSuccess) {
       cudaGetLastError();
       s = TC_ERR_OOM;
       break;
@@ -280,8 +294,8 @@ tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
     const uint32_t* d_src = src;
     const uint32_t* d_dst = dst;
     if (E > 0 && !edges_on_device) {
-      if (cudaMalloc(&staged_src, sizeof(uint32_t) * E) != cudaSuccess ||
-          cudaMalloc(&staged_dst, sizeof(uint32_t) * E) != cudaSuccess) {
+      if (dev_alloc(u, &staged_src, E, st) != cudaSuccess ||
+          dev_alloc(u, &staged_dst, E, st) != cudaSuccess) {
         cudaGetLastError();
         s = TC_ERR_OOM;
         break;
@@ -296,16 +310,17 @@ tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
     }
     const EdgeGroups grp{b->eoff, b->voff, d_nvert, b->k};
     if ((s = build_csr(u, d_src, d_dst, E, st, &grp)) != TC_OK) break;
-    if ((s = alloc_count_state(u)) != TC_OK) break;
+    if ((s = alloc_count_state(u, st)) != TC_OK) break;
     u->batch_k = b->k;
     u->voff = b->voff;
     u->gcount = b->gcount;
     if (cudaStreamSynchronize(st) != cudaSuccess) { s = TC_ERR_CUDA; break; }
   } while (0);
+  // the staging and group arrays go back in stream order after their last use
+  dev_free(b->u, staged_src, st);
+  dev_free(b->u, staged_dst, st);
+  dev_free(b->u, d_nvert, st);
   cudaStreamSynchronize(st);
-  cudaFree(staged_src);
-  cudaFree(staged_dst);
-  cudaFree(d_nvert);
   if (s != TC_OK) {
     free_batch(b);
     return s;
@@ -335,7 +350,6 @@ tc_status tc_batch_max_degree_vertices(tc_batch* b, void* stream, uint32_t* host
 
 tc_status tc_batch_destroy(tc_batch* b) {
   if (!b) return TC_OK;
-  cudaDeviceSynchronize();
   free_batch(b);
   return TC_OK;
 }

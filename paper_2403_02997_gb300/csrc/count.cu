@@ -778,9 +778,22 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         s_fail = force_sorted;
       }
       __syncthreads();
-      if (!force_sorted)
-        for (unsigned long long j = cb + threadIdx.x; j < ce; j += blockDim.x)
+      if (!force_sorted) {
+        // four loads in flight per thread before its inserts, instead of one
+        // dependent load latency per entry
+        unsigned long long j = cb + threadIdx.x;
+        for (; j + 3 * blockDim.x < ce; j += 4 * blockDim.x) {
+          const uint32_t w0 = col[j], w1 = col[j + blockDim.x], w2 = col[j + 2 * blockDim.x],
+                         w3 = col[j + 3 * blockDim.x];
+          bool ok = ck.insert(w0);
+          ok = ck.insert(w1) && ok;
+          ok = ck.insert(w2) && ok;
+          ok = ck.insert(w3) && ok;
+          if (!ok) s_fail = 1;
+        }
+        for (; j < ce; j += blockDim.x)
           if (!ck.insert(col[j])) s_fail = 1;
+      }
       __syncthreads();
       const bool sorted = s_fail != 0;
       if (sorted) {  // rare: keep the chunk as a sorted array instead
@@ -1090,11 +1103,11 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   TC_CUDA_TRY(cudaStreamSynchronize(st));
   const unsigned long long nitems = g->ctr_host->items;
   if (nitems > g->item_cap) {
-    cudaFree(g->item_owner);
+    dev_free(g, g->item_owner, st);
     g->item_owner = nullptr;
     g->item_cap = 0;
     const unsigned long long want = nitems + nitems / 4 + 1024;
-    TC_CUDA_TRY(cudaMalloc(&g->item_owner, sizeof(uint32_t) * want));
+    TC_CUDA_TRY(dev_alloc(g, &g->item_owner, want, st));
     g->item_cap = want;
   }
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
@@ -1182,9 +1195,9 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
 namespace {
 
 // Oriented adjacency storage (obeg[n+1], ocol[m]), allocated on first use.
-tc_status ensure_oriented(tc_graph* g) {
-  if (!g->obeg) TC_CUDA_TRY(cudaMalloc(&g->obeg, sizeof(unsigned long long) * ((size_t)g->n + 1)));
-  if (!g->ocol) TC_CUDA_TRY(cudaMalloc(&g->ocol, sizeof(uint32_t) * ((size_t)g->m + 1)));
+tc_status ensure_oriented(tc_graph* g, cudaStream_t st) {
+  if (!g->obeg) TC_CUDA_TRY(dev_alloc(g, &g->obeg, (size_t)g->n + 1, st));
+  if (!g->ocol) TC_CUDA_TRY(dev_alloc(g, &g->ocol, (size_t)g->m + 1, st));
   return TC_OK;
 }
 
@@ -1193,7 +1206,7 @@ tc_status orient(tc_graph* g, const unsigned long long* beg, const unsigned long
                  const uint32_t* arr, cudaStream_t st, unsigned long long* total) {
   const uint32_t n = g->n;
   const int sms = num_sms();
-  TC_TRY(ensure_oriented(g));
+  TC_TRY(ensure_oriented(g, st));
   k_row_degrees<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(beg, end, n, g->fdeg); TC_LAUNCHED();
   k_orient<<<sms * 16, 256, 0, st>>>(beg, end, arr, g->fdeg, n, g->ocount, nullptr, nullptr); TC_LAUNCHED();
   TC_TRY(exclusive_scan_u32(g->ocount, g->obeg, n, g->scan, st));

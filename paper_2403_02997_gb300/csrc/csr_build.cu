@@ -294,7 +294,7 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
 
   TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
   g->row_ptr = nullptr;
-  TC_CUDA_TRY(cudaMalloc(&g->row_ptr, sizeof(unsigned long long) * ((size_t)n + 1)));
+  TC_CUDA_TRY(dev_alloc(g, &g->row_ptr, (size_t)n + 1, st));
   if (N == 0) {
     TC_CUDA_TRY(cudaMemsetAsync(g->row_ptr, 0, sizeof(unsigned long long) * ((size_t)n + 1), st));
     g->nnz = 0;
@@ -304,15 +304,15 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
     const uint64_t ndb = (N + kDedupTile - 1) / kDedupTile;
     if (nb > 0x7FFFFFFFull) return TC_ERR_OVERFLOW;
     do {
-      if (cudaMalloc(&keys_a, sizeof(unsigned long long) * N) != cudaSuccess) { fail(TC_ERR_OOM); break; }
-      if (cudaMalloc(&keys_b, sizeof(unsigned long long) * N) != cudaSuccess) { fail(TC_ERR_OOM); break; }
-      if (cudaMalloc(&hist, sizeof(uint32_t) * kRadix * nb) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &keys_a, N, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &keys_b, N, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &hist, (size_t)kRadix * nb, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
       const uint64_t hcount = (uint64_t)kRadix * nb;
       const uint64_t off_entries = (hcount > ndb ? hcount : ndb) + 1;
-      if (cudaMalloc(&hoff, sizeof(unsigned long long) * off_entries) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &hoff, off_entries, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
       ScanScratch ss;
       ss.capacity = scan_scratch_entries(off_entries);
-      if (cudaMalloc(&ss.sums, sizeof(unsigned long long) * ss.capacity) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &ss.sums, ss.capacity, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
 
       if (groups)
         k_make_keys_multi<<<grid_for(E, kKeyTile, 152 * 64), 256, 0, st>>>(
@@ -330,15 +330,15 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
         keys_a = keys_b;
         keys_b = t;
       }
-      if (status != TC_OK) { cudaFree(ss.sums); break; }
+      if (status != TC_OK) { dev_free(g, ss.sums, st); break; }
       k_dedup_reduce<<<(unsigned)ndb, kDedupBlock, 0, st>>>(keys_a, N, hoff); TC_LAUNCHED();
-      if (exclusive_scan_u64(hoff, hoff, ndb, ss, st) != TC_OK) { cudaFree(ss.sums); fail(TC_ERR_CUDA); break; }
+      if (exclusive_scan_u64(hoff, hoff, ndb, ss, st) != TC_OK) { dev_free(g, ss.sums, st); fail(TC_ERR_CUDA); break; }
       unsigned long long nnz = 0;
       unsigned int err = 0;
       cudaMemcpyAsync(&nnz, hoff + ndb, sizeof(nnz), cudaMemcpyDeviceToHost, st);
       cudaMemcpyAsync(&err, &g->ctr->err, sizeof(err), cudaMemcpyDeviceToHost, st);
-      if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(ss.sums); fail(TC_ERR_CUDA); break; }
-      cudaFree(ss.sums);
+      if (cudaStreamSynchronize(st) != cudaSuccess) { dev_free(g, ss.sums, st); fail(TC_ERR_CUDA); break; }
+      dev_free(g, ss.sums, st);
       if (err & kErrVertexRange) { fail(TC_ERR_VERTEX_RANGE); break; }
       g->nnz = nnz;
       g->m = nnz / 2;
@@ -349,7 +349,7 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
       // padded to a multiple of 4 entries plus 4, so 16-byte loads of any
       // aligned quad that starts inside the array stay inside the allocation
       const size_t col_alloc = ((size_t)nnz + 7) & ~(size_t)3;
-      if (cudaMalloc(&g->col, sizeof(uint32_t) * col_alloc) != cudaSuccess) { fail(TC_ERR_OOM); break; }
+      if (dev_alloc(g, &g->col, col_alloc, st) != cudaSuccess) { fail(TC_ERR_OOM); break; }
       cudaMemsetAsync(g->col + nnz, 0, sizeof(uint32_t) * (col_alloc - nnz), st);
       k_dedup_write<<<(unsigned)ndb, kDedupBlock, 0, st>>>(keys_a, N, kb, n, hoff, hoff + ndb, g->col,
                                                            g->row_ptr); TC_LAUNCHED();
@@ -360,10 +360,10 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
       status = TC_ERR_CUDA;
     }
     cudaStreamSynchronize(st);
-    cudaFree(keys_a);
-    cudaFree(keys_b);
-    cudaFree(hist);
-    cudaFree(hoff);
+    dev_free(g, keys_a, st);
+    dev_free(g, keys_b, st);
+    dev_free(g, hist, st);
+    dev_free(g, hoff, st);
     if (status != TC_OK) return status;
   }
   // degree statistics: largest degree and the smallest vertex id that has it

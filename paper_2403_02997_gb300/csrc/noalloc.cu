@@ -196,7 +196,7 @@ tc_status na_levels(const unsigned long long* row_ptr, const uint32_t* col, int3
   for (int32_t lvl = 0; qlen > 0; ++lvl) {
     TC_CUDA_TRY(cudaMemsetAsync(s.next_n, 0, sizeof(unsigned long long), st));
     k_na_td<<<grid_for(qlen * 32, 256, sms * 8), 256, 0, st>>>(row_ptr, col, level, q, qlen,
-                                                             lvl + 1, nq, s.next_n);
+                                                             lvl + 1, nq, s.next_n); TC_LAUNCHED();
     TC_CUDA_TRY(cudaGetLastError());
     TC_TRY(read_u64(s.next_n, &qlen, st));
     uint32_t* t = q;
@@ -226,19 +226,19 @@ extern "C" tc_status tc_bfs_levels_noalloc(const uint64_t* row_ptr, const uint32
   // written before it is read (queues by appends, parents by k_na_cc_init,
   // counters by the memsets)
   TC_CUDA_TRY(cudaMemsetAsync(levels, 0xFF, sizeof(int32_t) * n, st));
-  k_na_root<<<1, 1, 0, st>>>(levels, s.queue_a, root);
+  k_na_root<<<1, 1, 0, st>>>(levels, s.queue_a, root); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_TRY(na_levels(rp, col, levels, 1, s, st));
   TC_CUDA_TRY(cudaMemsetAsync(s.unvisited, 0, sizeof(unsigned long long), st));
-  k_na_unvisited<<<sms * 8, 256, 0, st>>>(levels, n, s.unvisited);
+  k_na_unvisited<<<sms * 8, 256, 0, st>>>(levels, n, s.unvisited); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   unsigned long long left = 0;
   TC_TRY(read_u64(s.unvisited, &left, st));
   if (left == 0) return TC_OK;
-  k_na_cc_init<<<sms * 8, 256, 0, st>>>(s.parent, n);
-  k_na_cc_hook<<<sms * 16, 256, 0, st>>>(rp, col, levels, s.parent, n);
+  k_na_cc_init<<<sms * 8, 256, 0, st>>>(s.parent, n); TC_LAUNCHED();
+  k_na_cc_hook<<<sms * 16, 256, 0, st>>>(rp, col, levels, s.parent, n); TC_LAUNCHED();
   TC_CUDA_TRY(cudaMemsetAsync(s.next_n, 0, sizeof(unsigned long long), st));
-  k_na_cc_seed<<<sms * 8, 256, 0, st>>>(s.parent, levels, n, s.queue_a, s.next_n);
+  k_na_cc_seed<<<sms * 8, 256, 0, st>>>(s.parent, levels, n, s.queue_a, s.next_n); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   unsigned long long seeds = 0;
   TC_TRY(read_u64(s.next_n, &seeds, st));

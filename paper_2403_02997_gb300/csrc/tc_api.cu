@@ -3,6 +3,7 @@
 // of csr_build.cu, bfs.cu and count.cu.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -16,24 +17,88 @@ void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
 
 thread_local uint32_t g_launches = 0;
 
-int num_sms() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached = v > 0 ? v : 1;
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+int g_sms[kMaxDevices] = {};
+cudaMemPool_t g_pool[kMaxDevices] = {};
+cudaStream_t g_free_stream[kMaxDevices] = {};
+
+int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev >= 0 && dev < kMaxDevices ? dev : 0;
+}
+
+// The library's pool on the current device, created on first use.  Its
+// release threshold is the largest value, so memory freed into it stays
+// reserved for the next stream-ordered allocation instead of going back to
+// the driver at every synchronisation (tc_pool_trim returns it).
+cudaError_t lib_pool(cudaMemPool_t* pool) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ull;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pool[dev] = p;
   }
-  return cached;
+  *pool = g_pool[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+int num_sms() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  if (g_sms[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = v > 0 ? v : 1;
+  }
+  return g_sms[dev];
+}
+
+cudaStream_t free_stream() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  if (!g_free_stream[dev]) cudaStreamCreateWithFlags(&g_free_stream[dev], cudaStreamNonBlocking);
+  return g_free_stream[dev];
+}
+
+cudaError_t dev_malloc(const tc_graph* g, void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (g && g->pooled) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = lib_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+  }
+  return cudaMalloc(p, bytes);
+}
+
+void dev_free(const tc_graph* g, void* p, cudaStream_t st) {
+  if (!p) return;
+  if (g && g->pooled) cudaFreeAsync(p, st);
+  else cudaFree(p);
 }
 
 namespace {
 
 template <typename T>
-tc_status dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+tc_status dalloc(const tc_graph* g, T** p, size_t count, cudaStream_t st) {
+  cudaError_t e = dev_alloc(g, p, count, st);
   if (e != cudaSuccess) {
     set_last_cuda_error(e);
     cudaGetLastError();
@@ -51,38 +116,43 @@ void free_graph(tc_graph* g) {
                   g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums,
                   g->lcol,    g->lsplit, g->tile_row, g->tile_cnt, g->medium, g->obeg,
                   g->ocol};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (g->ctr_host) cudaFreeHost(g->ctr_host);
+  // every call on the handle finished its work before returning: nothing is
+  // pending on this memory, so pooled memory goes back on the library's stream
+  cudaStream_t fs = g->pooled ? free_stream() : nullptr;
+  for (void* p : ptrs) dev_free(g, p, fs);
+  if (g->ctr_host) {
+    if (g->pooled) delete g->ctr_host;
+    else cudaFreeHost(g->ctr_host);
+  }
   for (cudaEvent_t e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
 }
 
-tc_status alloc_count_state(tc_graph* g) {
+tc_status alloc_count_state(tc_graph* g, cudaStream_t st) {
   const size_t n = g->n, m = g->m;
-  TC_TRY(dalloc(&g->level, n));
-  TC_TRY(dalloc(&g->queue_a, n));
-  TC_TRY(dalloc(&g->queue_b, n));
-  TC_TRY(dalloc(&g->qoff, n + 1));
-  TC_TRY(dalloc(&g->ooff, n + 1));
-  TC_TRY(dalloc(&g->ioff, n + 1));
-  TC_TRY(dalloc(&g->parent, n));
-  TC_TRY(dalloc(&g->fdeg, n));
-  TC_TRY(dalloc(&g->ocount, n));
-  TC_TRY(dalloc(&g->ofill, n));
-  TC_TRY(dalloc(&g->cover, m));
-  TC_TRY(dalloc(&g->large, m));
-  TC_TRY(dalloc(&g->ostream, m));
-  TC_TRY(dalloc(&g->medium, m));
-  TC_TRY(dalloc(&g->lcol, g->nnz));
-  TC_TRY(dalloc(&g->lsplit, n));
+  TC_TRY(dalloc(g, &g->level, n, st));
+  TC_TRY(dalloc(g, &g->queue_a, n, st));
+  TC_TRY(dalloc(g, &g->queue_b, n, st));
+  TC_TRY(dalloc(g, &g->qoff, n + 1, st));
+  TC_TRY(dalloc(g, &g->ooff, n + 1, st));
+  TC_TRY(dalloc(g, &g->ioff, n + 1, st));
+  TC_TRY(dalloc(g, &g->parent, n, st));
+  TC_TRY(dalloc(g, &g->fdeg, n, st));
+  TC_TRY(dalloc(g, &g->ocount, n, st));
+  TC_TRY(dalloc(g, &g->ofill, n, st));
+  TC_TRY(dalloc(g, &g->cover, m, st));
+  TC_TRY(dalloc(g, &g->large, m, st));
+  TC_TRY(dalloc(g, &g->ostream, m, st));
+  TC_TRY(dalloc(g, &g->medium, m, st));
+  TC_TRY(dalloc(g, &g->lcol, g->nnz, st));
+  TC_TRY(dalloc(g, &g->lsplit, n, st));
   // tiles of rows longer than 4096 entries, 4096 per tile: at most nnz / 2048
   g->tile_cap = g->nnz / 2048 + 1;
-  TC_TRY(dalloc(&g->tile_row, g->tile_cap));
-  TC_TRY(dalloc(&g->tile_cnt, g->tile_cap));
+  TC_TRY(dalloc(g, &g->tile_row, g->tile_cap, st));
+  TC_TRY(dalloc(g, &g->tile_cnt, g->tile_cap, st));
   g->scan.capacity = scan_scratch_entries(n + 1);
-  TC_TRY(dalloc(&g->scan.sums, g->scan.capacity));
+  TC_TRY(dalloc(g, &g->scan.sums, g->scan.capacity, st));
   return TC_OK;
 }
 
@@ -156,7 +226,7 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
   uint32_t* staged_src = nullptr;
   uint32_t* staged_dst = nullptr;
   do {
-    if ((s = dalloc(&g->ctr, 1)) != TC_OK) break;
+    if ((s = dalloc(g, &g->ctr, 1, st)) != TC_OK) break;
     if (cudaMallocHost(reinterpret_cast<void**>(&g->ctr_host), sizeof(DevCounters)) != cudaSuccess) {
       s = TC_ERR_OOM;
       break;
@@ -168,8 +238,8 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
     const uint32_t* d_src = src;
     const uint32_t* d_dst = dst;
     if (num_edges > 0 && !edges_on_device) {
-      if ((s = dalloc(&staged_src, num_edges)) != TC_OK) break;
-      if ((s = dalloc(&staged_dst, num_edges)) != TC_OK) break;
+      if ((s = dalloc(g, &staged_src, num_edges, st)) != TC_OK) break;
+      if ((s = dalloc(g, &staged_dst, num_edges, st)) != TC_OK) break;
       if (cudaMemcpyAsync(staged_src, src, sizeof(uint32_t) * num_edges, cudaMemcpyHostToDevice, st) != cudaSuccess ||
           cudaMemcpyAsync(staged_dst, dst, sizeof(uint32_t) * num_edges, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         s = TC_ERR_CUDA;
@@ -179,7 +249,7 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
       d_dst = staged_dst;
     }
     if ((s = build_csr(g, d_src, d_dst, num_edges, st)) != TC_OK) break;
-    if ((s = alloc_count_state(g)) != TC_OK) break;
+    if ((s = alloc_count_state(g, st)) != TC_OK) break;
     s = sync_status(g, st);
   } while (0);
   if (staged_src || staged_dst) {
@@ -197,8 +267,27 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
 
 tc_status tc_graph_destroy(tc_graph* g) {
   if (!g) return TC_OK;
-  cudaDeviceSynchronize();
+  // every call on the handle synchronised its own stream before returning, so
+  // no work on its memory is pending: no device-wide synchronisation here
   free_graph(g);
+  return TC_OK;
+}
+
+tc_status tc_pool_trim(uint64_t keep_bytes) {
+  cudaMemPool_t pool = nullptr;
+  TC_CUDA_TRY(lib_pool(&pool));
+  TC_CUDA_TRY(cudaStreamSynchronize(free_stream()));
+  TC_CUDA_TRY(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+  return TC_OK;
+}
+
+tc_status tc_pool_reserved(uint64_t* bytes) {
+  if (!bytes) return TC_ERR_INVALID_ARG;
+  cudaMemPool_t pool = nullptr;
+  TC_CUDA_TRY(lib_pool(&pool));
+  unsigned long long v = 0;
+  TC_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v));
+  *bytes = v;
   return TC_OK;
 }
 

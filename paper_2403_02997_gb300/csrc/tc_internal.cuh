@@ -111,6 +111,12 @@ struct tc_graph {
   tc_stats stats;
   bool counted = false;
   uint32_t last_root = 0;
+  // pooled: device memory comes stream-ordered from the library's pool and is
+  // returned without synchronising the device (batches built from edge lists,
+  // which a serving loop creates and destroys while other work runs); the
+  // counter mirror is then pageable host memory (freeing pinned memory would
+  // synchronise the device)
+  bool pooled = false;
 };
 
 namespace tc {
@@ -147,6 +153,22 @@ inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap = 1u <<
 
 int num_sms();
 
+// Device memory of handle g (g may be NULL: plain).  A pooled handle's memory
+// is taken from the library's per-device pool in stream order on `st` and
+// freed in stream order (cudaFreeAsync); other memory uses cudaMalloc /
+// cudaFree.  dev_free ignores NULL.
+cudaError_t dev_malloc(const tc_graph* g, void** p, size_t bytes, cudaStream_t st);
+void dev_free(const tc_graph* g, void* p, cudaStream_t st);
+template <typename T>
+cudaError_t dev_alloc(const tc_graph* g, T** p, size_t count, cudaStream_t st) {
+  *p = nullptr;
+  return dev_malloc(g, reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1), st);
+}
+// A non-blocking stream of the current device owned by the library, on which
+// destroy calls return pooled memory (every call on a handle has finished its
+// work before it returns, so nothing is pending on that memory).
+cudaStream_t free_stream();
+
 // Device-wide exclusive scan of `count` values (uint32 or uint64 input) into
 // uint64 offsets out[0..count]; out[count] holds the total.  `in` and `out`
 // may alias only for the uint64 variant.
@@ -177,7 +199,7 @@ int key_bits(uint32_t n);
 // BFS from the k roots already stored in queue_a (all at level 0, level[] set
 // to -1 elsewhere by the caller), then the restart rule.
 tc_status run_bfs_from_queue(tc_graph* g, uint64_t k, cudaStream_t st);
-tc_status alloc_count_state(tc_graph* g);
+tc_status alloc_count_state(tc_graph* g, cudaStream_t st);
 void free_graph(tc_graph* g);
 void params_default(tc_params* p);
 

@@ -13,7 +13,12 @@ rule).
   returns to the budget for the next admissions.
 
 While a batch is on the device, newly arrived graphs are being admitted and built for the next one.
-Building and counting overlap; a request never waits for a fixed batch size.
+Building and counting overlap on the device: the batch's memory, sort buffers included, comes
+stream-ordered from the library's pool and goes back without a device-wide synchronisation, and
+the edge lists are staged in page-locked host memory, so neither thread's copies, allocations or
+frees wait for the other's kernels. The server records every build and count interval;
+``overlap_stats`` reports how much of the build time ran while a count was in progress. A request
+never waits for a fixed batch size.
 
 Latency is measured from arrival to the moment the count is on the host; p50 / p99 come from the
 completed requests.
@@ -74,10 +79,12 @@ class GpuBackend:
         self.params = dict(params or {})
         self.build_stream = torch.cuda.Stream()
         self.count_stream = torch.cuda.Stream()
+        self.staging = tc.PinnedStaging()   # used by the admission thread only
 
     def build(self, group):
         """One batch straight from the group's edge lists; returns (batch, roots)."""
-        b = tc.Batch.from_edges([(r.src, r.dst, r.n) for r in group], stream=self.build_stream)
+        b = tc.Batch.from_edges([(r.src, r.dst, r.n) for r in group], stream=self.build_stream,
+                                staging=self.staging)
         if self.params:
             b.set_params(**self.params)
         md = b.max_degree_vertices(stream=self.build_stream)
@@ -103,6 +110,8 @@ class Server:
         self.peak_used = 0
         self.completed: List[Request] = []
         self.batches: List[int] = []
+        self.build_spans: List[tuple] = []   # (start, end) of each batch build, host clock
+        self.count_spans: List[tuple] = []   # (start, end) of each batch count
         self.stopping = False
         self.threads = [threading.Thread(target=self._admit_loop, daemon=True),
                         threading.Thread(target=self._count_loop, daemon=True)]
@@ -149,8 +158,11 @@ class Server:
                 continue
             try:
                 # one device build for the whole group: a batch straight from the edge lists
+                t0 = time.perf_counter()
                 b, roots = self.backend.build(group)
+                t1 = time.perf_counter()
                 with self.lock:
+                    self.build_spans.append((t0, t1))
                     self.ready.append((group, b, roots))
                     self.lock.notify_all()
             except Exception as e:  # the group fails; its memory returns
@@ -171,10 +183,12 @@ class Server:
                 if not self.ready and self.stopping and not self.pending:
                     return
                 reqs, b, roots = self.ready.pop(0)
+            t0 = time.perf_counter()
             try:
                 counts, err = self.backend.count(b, roots), None
             except Exception as e:
                 counts, err = [None] * len(reqs), str(e)
+            t1 = time.perf_counter()
             self.backend.release(b)
             now = time.perf_counter()
             for r, c in zip(reqs, counts):
@@ -184,7 +198,48 @@ class Server:
                 self.used -= sum(r.bytes for r in reqs)
                 self.completed.extend(reqs)
                 self.batches.append(len(reqs))
+                self.count_spans.append((t0, t1))
                 self.lock.notify_all()
+
+    # -- measurement ----------------------------------------------------------
+    def overlap_stats(self) -> dict:
+        """How much building and counting ran at the same time (host clock intervals).
+
+        build_s / count_s: total time in batch builds / batch counts; overlap_s: the time in
+        which a build and a count were both in progress; build_overlap_frac = overlap_s /
+        build_s (1.0: every build ran while a count was on the device).
+        """
+        with self.lock:
+            builds, counts = list(self.build_spans), list(self.count_spans)
+        return overlap_of(builds, counts)
+
+
+def overlap_of(builds, counts) -> dict:
+    """Total lengths of two interval lists and of their intersection."""
+    def merged(spans):
+        out = []
+        for a, b in sorted(spans):
+            if out and a <= out[-1][1]:
+                out[-1][1] = max(out[-1][1], b)
+            else:
+                out.append([a, b])
+        return out
+    mb, mc = merged(builds), merged(counts)
+    i = j = 0
+    both = 0.0
+    while i < len(mb) and j < len(mc):
+        lo, hi = max(mb[i][0], mc[j][0]), min(mb[i][1], mc[j][1])
+        if hi > lo:
+            both += hi - lo
+        if mb[i][1] < mc[j][1]:
+            i += 1
+        else:
+            j += 1
+    build_s = sum(b - a for a, b in mb)
+    count_s = sum(b - a for a, b in mc)
+    return {"builds": len(builds), "counts": len(counts), "build_s": build_s,
+            "count_s": count_s, "overlap_s": both,
+            "build_overlap_frac": both / build_s if build_s > 0 else None}
 
 
 def percentile(xs, q):

@@ -13,21 +13,35 @@ from paper_2403_02997_gb300 import gen
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_threaded_sample_equals_one_call():
-    """The sampler's threads each run the oracle's edge loop on a slice of the
-    sample; their sum is the single-call count (and, over all of S, T)."""
+def test_sampler_baselines():
+    """One sample times both oracle forms; each full-graph estimate is the BFS and scan time
+    plus the sampled seconds per cover edge times |S|, and the OpenMP form reports the host's
+    thread count."""
     spec = gen.rmat_spec(12, 16, 5)
     src, dst = spec.edges()
-    one = bench.OracleSampler(spec, src, dst, 0, target_s=1.0, cores=1)
-    many = bench.OracleSampler(spec, src, dst, 0, target_s=1.0, cores=4)
-    lv = oracle.bfs_levels(one.rp, one.col, 0)
-    cov = oracle.cetc(one.rp, one.col, lv, want_cover=True)
-    us, vs = cov["cover_u"], cov["cover_v"]
-    assert one._edges(lv, us, vs) == many._edges(lv, us, vs) == cov["T"]
-    idx = np.random.default_rng(3).integers(0, us.size, 999)
-    assert one._edges(lv, us[idx], vs[idx]) == many._edges(lv, us[idx], vs[idx])
-    r = many.step()
-    assert r["edges"] == one.m and r["est_seconds"] > 0 and r["done"] > 0
+    sam = bench.OracleSampler(spec, src, dst, 0, target_s=0.5)
+    r = sam.step()
+    lv = oracle.bfs_levels(sam.rp, sam.col, 0)
+    assert r["num_cover"] == oracle.cetc(sam.rp, sam.col, lv)["num_cover"]
+    for name, cores in (("seq", 1), ("omp", oracle.num_threads())):
+        b = r[name]
+        assert b["cores"] == cores and b["sampled_edges"] > 0 and b["sample_s"] > 0
+        est = r["bfs_s"] + r["scan_s"] + b["sample_s"] / b["sampled_edges"] * r["num_cover"]
+        assert abs(b["est_full_seconds"] - est) <= 1e-9 * est
+        assert abs(b["value"] - sam.m / est) <= 1e-9 * b["value"]
+    base = sam.baseline(r)
+    assert base["kind"] == "oracle" and base["value"] == r["omp"]["value"]
+    assert base["seq"]["cores"] == 1 and base["sample_wall_s"] >= r["omp"]["sample_s"]
+
+
+def test_estimate_validation_runs():
+    spec = gen.rmat_spec(12, 16, 5)
+    src, dst = spec.edges()
+    v = bench.validate_cpu_estimate(spec, src, dst, 0, 0.3)
+    rp, col = oracle.build_csr(spec.n, src, dst)
+    assert v["triangles"] == oracle.forward(rp, col)     # the full run counts every triangle
+    assert v["full_seconds"] > 0 and v["estimated_seconds"] > 0
+    assert v["relative_error"] == (v["estimated_seconds"] - v["full_seconds"]) / v["full_seconds"]
 
 
 def test_reference_arm_line():
@@ -39,3 +53,7 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["unit"] == "edges/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["metric"] == bench.METRIC
+    # the step time is the sample's measured wall time, the extrapolation is reported apart
+    assert line["est_full_seconds"] > 0 and line["ms_per_step"] > 0
+    assert abs(line["value"] - line["cpu_baseline"]["value"]) <= 1e-9 * line["value"]
+    assert {"seq", "omp"} <= set(line["cpu_baseline"])

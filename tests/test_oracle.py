@@ -296,6 +296,29 @@ def test_edge_list_count_equals_full_loop():
     assert half["T"] + other["T"] == full["T"]
 
 
+def test_parallel_edge_list_count():
+    """The OpenMP edge loop (CETC-SM's form) sums the same per-edge counts: over all of S it
+    gives C(n, 3) on K_n and the full loop's T, c1, c2 on an R-MAT graph; on a random subset it
+    equals the single-thread loop."""
+    k = 23
+    s, d = zip(*[(a, b) for a in range(k) for b in range(a + 1, k)])
+    rp, col = oracle.build_csr(k, np.array(s, np.uint32), np.array(d, np.uint32))
+    lv = oracle.bfs_levels(rp, col, 0)
+    full = oracle.cetc(rp, col, lv, want_cover=True)
+    par = oracle.cetc_sm_edges(rp, col, lv, full["cover_u"], full["cover_v"])
+    assert par["T"] == comb(k, 3)
+    n = 1 << 11
+    s, d = gen.rmat_edges(11, 8, 6)
+    rp, col = oracle.build_csr(n, s, d)
+    lv = oracle.bfs_levels(rp, col, 0)
+    full = oracle.cetc(rp, col, lv, want_cover=True)
+    par = oracle.cetc_sm_edges(rp, col, lv, full["cover_u"], full["cover_v"])
+    assert (par["T"], par["c1"], par["c2"]) == (full["T"], full["c1"], full["c2"])
+    idx = np.random.default_rng(3).integers(0, full["num_cover"], size=500)
+    u, v = full["cover_u"][idx], full["cover_v"][idx]
+    assert oracle.cetc_sm_edges(rp, col, lv, u, v) == oracle.cetc_edges(rp, col, lv, u, v)
+
+
 def test_root_invariance_and_sampling():
     n = 1 << 10
     s, d = gen.rmat_edges(10, 8, 77)

@@ -38,6 +38,50 @@ def test_results_alone_and_in_the_mix():
     assert res["p99_ms"] >= res["p50_ms"] > 0
 
 
+@pytest.mark.gpu
+def test_device_memory_of_a_batch_within_footprint():
+    """The device memory a request really takes (free-memory delta around one build and count
+    of a group, with the pool keeping the build's peak reserved) stays within footprint_bytes,
+    the bound admission charges against the HBM budget."""
+    import torch
+
+    import paper_2403_02997_gb300 as tc
+    from paper_2403_02997_gb300 import build, serve
+    build.build_all()
+    specs = gen.batched_specs(32, master_seed=12, log2_min=8, log2_max=14)
+    graphs = [(*sp.edges(), sp.n, None if sp.root == "maxdeg" else 0) for sp in specs]
+    graphs += [(*gen.rmat_edges(17, 16, 30 + i), 1 << 17, None) for i in range(3)]
+    reqs = [serve.Request(rid=i, src=s, dst=d, n=n, root=r) for i, (s, d, n, r) in enumerate(graphs)]
+    backend = serve.GpuBackend()
+    b, roots = backend.build(reqs[:4])       # warm-up: kernels loaded, pool and streams made
+    backend.count(b, roots)
+    backend.release(b)
+    torch.cuda.synchronize()
+    tc.pool_trim(0)
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    b, roots = backend.build(reqs)
+    counts = backend.count(b, roots)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    reserved = tc.pool_reserved()
+    backend.release(b)
+    torch.cuda.synchronize()
+    tc.pool_trim(0)
+    assert len(counts) == len(reqs) and all(c >= 0 for c in counts)
+    bound = sum(serve.footprint_bytes(r.n, int(r.src.size)) for r in reqs)
+    assert 0 < used <= bound, (used, bound)
+    assert reserved <= bound, (reserved, bound)
+
+
+def test_overlap_of_intervals():
+    from paper_2403_02997_gb300.serve import overlap_of
+    r = overlap_of([(0.0, 2.0), (5.0, 6.0)], [(1.0, 3.0), (3.5, 5.5)])
+    assert r["build_s"] == 3.0 and r["count_s"] == 4.0
+    assert abs(r["overlap_s"] - 1.5) < 1e-12 and abs(r["build_overlap_frac"] - 0.5) < 1e-12
+    assert overlap_of([], [(0.0, 1.0)])["overlap_s"] == 0.0
+
+
 class OracleBackend:
     """A host stand-in for the device (the oracle counts each graph), so the
     serving loop's admission, grouping and answering run without a GPU."""
@@ -95,6 +139,9 @@ def test_admission_respects_budget_and_answers_everything():
     assert max(srv.batches) > 1 and max(srv.batches) <= 6      # grouped, never above max_batch
     assert be.released == len(srv.batches)
     assert res["p99_ms"] >= res["p50_ms"] > 0
+    ov = srv.overlap_stats()          # every build and count interval was recorded
+    assert ov["builds"] == ov["counts"] == len(srv.batches)
+    assert 0.0 <= ov["overlap_s"] <= min(ov["build_s"], ov["count_s"])
 
 
 def test_oversized_request_and_failed_build():

@@ -3,12 +3,14 @@
 For callers that cannot call cudaMalloc, tc_bfs_levels_noalloc computes BFS
 levels of a device CSR they own, using only a fixed scratch array compiled
 into the library.  Its levels must equal those of tc_count + tc_get_levels on
-the same graph and root, on consecutive calls (the scratch array keeps what the
-previous call left in it).  Integer output: compared exactly.
+the same graph and root, and those of the CPU oracle's BFS, on consecutive calls
+(the scratch array keeps what the previous call left in it).  Integer output:
+compared exactly.
 """
 import numpy as np
 import pytest
 
+import oracle
 import paper_2403_02997_gb300 as tc
 from paper_2403_02997_gb300 import gen
 from tests import graphs
@@ -52,6 +54,8 @@ def test_noalloc_levels_match_tc_count_on_consecutive_calls():
     for src, dst, n, root in cases:
         got, want = _levels_both_ways(src, dst, n, root)
         assert np.array_equal(got, want)
+        rp, col = oracle.build_csr(n, src, dst)
+        assert np.array_equal(got, oracle.bfs_levels(rp, col, root))
 
 
 def test_noalloc_rejects_oversized_graph():
