@@ -84,6 +84,50 @@ __device__ __forceinline__ uint32_t row_of(const unsigned long long* row_ptr, ui
   return lo;
 }
 
+// Four ids of a sorted row from position p on, kEmpty past its end e (four
+// independent loads).
+__device__ __forceinline__ void load4(const uint32_t* __restrict__ col, unsigned long long p,
+                                      unsigned long long e, uint32_t& w0, uint32_t& w1,
+                                      uint32_t& w2, uint32_t& w3) {
+  w0 = p < e ? col[p] : kEmpty;
+  w1 = p + 1 < e ? col[p + 1] : kEmpty;
+  w2 = p + 2 < e ? col[p + 2] : kEmpty;
+  w3 = p + 3 < e ? col[p + 3] : kEmpty;
+}
+
+// The two-pointer merge of Algorithm EMP over the sorted rows arr[ba, ea) and
+// arr[bb, eb), taken four ids at a time on each side: all 16 pairs of the two
+// current blocks are compared, then the block whose last id is smaller moves
+// on (both on a tie) with its next four ids loaded together.  A plain merge
+// waits for one dependent load per step; this one for one per four ids.
+// Every common id w is reported once, by hit(w): a block moves past w only
+// after the other row's block that holds w has been current (its last id
+// would otherwise be below w, and the smaller-last rule would have moved it
+// instead).  Ids are below 2^31, so kEmpty past a row's end matches nothing.
+template <typename Hit>
+__device__ __forceinline__ void block_merge(const uint32_t* __restrict__ arr, unsigned long long ba,
+                                            unsigned long long ea, unsigned long long bb,
+                                            unsigned long long eb, Hit&& hit) {
+  uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+  load4(arr, ba, ea, a0, a1, a2, a3);
+  load4(arr, bb, eb, b0, b1, b2, b3);
+  while (ba < ea && bb < eb) {
+    if (a0 == b0 || a0 == b1 || a0 == b2 || a0 == b3) hit(a0);
+    if (a1 != kEmpty && (a1 == b0 || a1 == b1 || a1 == b2 || a1 == b3)) hit(a1);
+    if (a2 != kEmpty && (a2 == b0 || a2 == b1 || a2 == b2 || a2 == b3)) hit(a2);
+    if (a3 != kEmpty && (a3 == b0 || a3 == b1 || a3 == b2 || a3 == b3)) hit(a3);
+    const bool step_a = a3 <= b3, step_b = b3 <= a3;
+    if (step_a) {
+      ba += 4;
+      load4(arr, ba, ea, a0, a1, a2, a3);
+    }
+    if (step_b) {
+      bb += 4;
+      load4(arr, bb, eb, b0, b1, b2, b3);
+    }
+  }
+}
+
 // c1 and c2' of one thread (see the file comment).
 struct Tally {
   unsigned long long c1 = 0, c2c = 0;
@@ -191,27 +235,17 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
             const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
             const unsigned long long du = eu - bu, dv = ev - bv;
             if (du <= small_max && dv <= small_max) {
-              // two-pointer merge of N(u) and N(v)
-              unsigned long long x = bu, y = bv;
+              // merge of N(u) and N(v) (blocked two-pointer merge)
               uint32_t here = 0;
-              while (x < eu && y < ev) {
-                const uint32_t a = col[x], c = col[y];
-                if (a == c) {
-                  if (level[a] != lu) {
-                    ++tl.c1;
-                    ++here;
-                  } else if (v < a) {
-                    ++tl.c2c;
-                    ++here;
-                  }
-                  ++x;
-                  ++y;
-                } else if (a < c) {
-                  ++x;
-                } else {
-                  ++y;
+              block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
+                if (level[w] != lu) {
+                  ++tl.c1;
+                  ++here;
+                } else if (v < w) {
+                  ++tl.c2c;
+                  ++here;
                 }
-              }
+              });
               if (kEmit && here) {
                 // the same merge again, writing this edge's triangles to the
                 // slots reserved for them
@@ -220,28 +254,17 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                   atomicAdd(&em.vcount[u], (unsigned long long)here);
                   atomicAdd(&em.vcount[v], (unsigned long long)here);
                 }
-                x = bu;
-                y = bv;
-                while (x < eu && y < ev) {
-                  const uint32_t a = col[x], c = col[y];
-                  if (a == c) {
-                    if (level[a] != lu || v < a) {
-                      if (em.tri && pos < em.cap) {
-                        em.tri[3 * pos] = u;
-                        em.tri[3 * pos + 1] = v;
-                        em.tri[3 * pos + 2] = a;
-                      }
-                      ++pos;
-                      if (em.vcount) atomicAdd(&em.vcount[a], 1ull);
+                block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
+                  if (level[w] != lu || v < w) {
+                    if (em.tri && pos < em.cap) {
+                      em.tri[3 * pos] = u;
+                      em.tri[3 * pos + 1] = v;
+                      em.tri[3 * pos + 2] = w;
                     }
-                    ++x;
-                    ++y;
-                  } else if (a < c) {
-                    ++x;
-                  } else {
-                    ++y;
+                    ++pos;
+                    if (em.vcount) atomicAdd(&em.vcount[w], 1ull);
                   }
-                }
+                });
               }
               if (nb && here) {
                 const uint32_t gid = s_g0 == s_g1 ? s_g0 : batch_graph_of(voff, s_g0, s_g1, u);
@@ -938,14 +961,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_forward_pairs(
         const unsigned long long dx = ex - bx, dw = ew - bw;
         if (dw > 0) {
           if (dx <= small_max && dw <= small_max) {
-            unsigned long long p = bx, q = bw;
             uint32_t here = 0;
-            while (p < ex && q < ew) {
-              const uint32_t a = ocol[p], c = ocol[q];
-              here += a == c;
-              p += a <= c;
-              q += c <= a;
-            }
+            block_merge(ocol, bx, ex, bw, ew, [&](uint32_t) { ++here; });
             if (as_c2) tl.c2c += here; else tl.c1 += here;
           } else {
             is_large = true;
@@ -1000,14 +1017,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
           const unsigned long long du = eu - bu, dv = ev - bv;
           if (du > 0 && dv > 0) {
             if (du <= small_max && dv <= small_max) {
-              unsigned long long p = bu, q = bv;
               uint32_t here = 0;
-              while (p < eu && q < ev) {
-                const uint32_t a = lcol[p], c = lcol[q];
-                here += a == c;
-                p += a <= c;
-                q += c <= a;
-              }
+              block_merge(lcol, bu, eu, bv, ev, [&](uint32_t) { ++here; });
               tl.c1 += here;
             } else {
               is_large = true;
