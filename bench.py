@@ -523,6 +523,19 @@ def run_ours(args, world, rank, local):
     assert fe_count == T
     variants["cetc_seq_fe_0.7"] = {"covering_ratio": n_cover / max(m, 1),
                                    "ran": "forward" if fe_forward else "cetc_seq"}
+    # CETC-Seq-FE with the threshold the autotuner learned for this graph family
+    fe_thr = None if args.no_tuned else autotune.lookup_fe(
+        autotune.signature(spec.n, g.m, g.d_max, spec.family))
+    if fe_thr is not None:
+        ms = []
+        for _ in range(3):
+            fe_count, fe_forward = g.count_fe(root, fe_thr, stream=stream)
+            assert fe_count == T
+            ms.append(g.stats()["ms_total"])
+        variants["cetc_seq_fe_learned"] = {
+            "threshold": fe_thr, "covering_ratio": n_cover / max(m, 1),
+            "ran": "forward" if fe_forward else "cetc_seq", "ms": statistics.median(ms),
+            "edges_per_s": m / (statistics.median(ms) / 1e3)}
     peak, peak_kind = measured_peaks()
     hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
     achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0

@@ -15,6 +15,12 @@ CUDA-event totals (``ms_total`` of tc_stats), and the best of ``trials`` runs is
 
 Results are cached in a JSON table keyed by a workload signature: family, log2 n, log2 m,
 log2 d_max, and batch size. ``lookup`` returns the tuned parameters for a signature, or None.
+
+``learn_fe_threshold`` learns Algorithm CETC-Seq-FE's switch point for a graph family: the
+variant takes the forward count when the covering ratio c = |S| / m after the BFS is at least
+the threshold (the paper fixes 0.7). It times the cover-edge count and the forward count on a
+graph of the family and puts the threshold just below that graph's c when the forward count
+was faster, just above it otherwise; ``lookup_fe`` returns it for a signature.
 """
 from __future__ import annotations
 
@@ -94,6 +100,42 @@ def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials:
             "seconds": time.time() - t0}
 
 
+def learn_fe_threshold(graph, root, trials: int = 2, margin: float = 0.05) -> dict:
+    """CETC-Seq-FE's threshold for the family of `graph` (a tc.Graph, or any object with
+    count(root), count_forward(), stats() and m)."""
+    def best(fn):
+        ms, val = float("inf"), None
+        for _ in range(trials):
+            v = fn()
+            if val is not None and v != val:
+                raise RuntimeError("count changed between runs")
+            val = v
+            ms = min(ms, float(graph.stats()["ms_total"]))
+        return ms, val
+    ms_cetc, t_cetc = best(lambda: graph.count(root))
+    c = graph.stats()["num_cover"] / max(int(graph.m), 1)
+    ms_fwd, t_fwd = best(lambda: graph.count_forward())
+    if t_fwd != t_cetc:
+        raise RuntimeError(f"forward count {t_fwd} != cover-edge count {t_cetc}")
+    forward_wins = ms_fwd < ms_cetc
+    thr = c * (1.0 - margin) if forward_wins else c * (1.0 + margin)
+    return {"threshold": thr, "covering_ratio": c, "ms_cetc": ms_cetc, "ms_forward": ms_fwd,
+            "forward_faster": forward_wins}
+
+
+def store_fe(sig: str, fe: dict, path: str = CACHE) -> None:
+    table = load_cache(path)
+    table.setdefault(sig, {})["fe"] = fe
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
+def lookup_fe(sig: str, path: str = CACHE) -> Optional[float]:
+    entry = load_cache(path).get(sig, {}).get("fe")
+    return None if entry is None else float(entry["threshold"])
+
+
 def load_cache(path: str = CACHE) -> dict:
     if os.path.exists(path):
         with open(path) as f:
@@ -103,8 +145,8 @@ def load_cache(path: str = CACHE) -> dict:
 
 def store(sig: str, result: dict, path: str = CACHE) -> None:
     table = load_cache(path)
-    table[sig] = {"params": result["params"], "ms": result["ms"],
-                  "default_ms": result["default_ms"]}
+    table.setdefault(sig, {}).update({"params": result["params"], "ms": result["ms"],
+                                      "default_ms": result["default_ms"]})
     with open(path, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
         f.write("\n")
@@ -112,7 +154,7 @@ def store(sig: str, result: dict, path: str = CACHE) -> None:
 
 def lookup(sig: str, path: str = CACHE) -> Optional[dict]:
     entry = load_cache(path).get(sig)
-    return None if entry is None else dict(entry["params"])
+    return None if entry is None or "params" not in entry else dict(entry["params"])
 
 
 if __name__ == "__main__":
@@ -130,6 +172,8 @@ if __name__ == "__main__":
     ap.add_argument("--trials", type=int, default=2)
     ap.add_argument("--budget", type=float, default=150.0)
     ap.add_argument("--out", default=CACHE, help="table to update (default: the package's)")
+    ap.add_argument("--fe", action="store_true",
+                    help="learn CETC-Seq-FE's threshold for single-graph workloads (no descent)")
     args = ap.parse_args()
     build.build_all()
     specs = {"rmat24": gen.RMAT_24, "rmat22": gen.rmat_spec(22, 16, 2), "mesh4096": gen.MESH_4096,
@@ -151,6 +195,12 @@ if __name__ == "__main__":
                               torch.from_numpy(dst.view(np.int32)).cuda(), s.n)
             roots = target.max_degree_vertex() if s.root == "maxdeg" else 0
             sig = signature(s.n, target.m, target.d_max, s.family)
+        if args.fe and w != "batched":
+            fe = learn_fe_threshold(target, roots, trials=args.trials)
+            store_fe(sig, fe, args.out)
+            print(json.dumps({"workload": w, "signature": sig, "fe": fe}), flush=True)
+            target.close()
+            continue
         res = tune(target, roots, trials=args.trials, time_budget_s=args.budget)
         store(sig, res, args.out)
         print(json.dumps({"workload": w, "signature": sig, "params": res["params"],

@@ -184,9 +184,60 @@ struct Emit {
   }
 };
 
+// The small bin (both degrees <= small_max), compacted: k_cover queues these
+// cover edges per warp (ballot ranks into shared memory) and, once 32 are
+// queued, every lane merges one of them (block_merge).  Without the queue
+// only the lanes whose entry happened to be a small cover edge -- about a
+// quarter of them -- would merge while the rest of the warp waited.  A
+// common neighbour w counts as in Algorithm CETC-Seq: c1 when L(w) != L(u),
+// c2' when L(w) == L(u) and v < w.  In batch mode the hits go to u's graph.
+constexpr int kSmallQueue = 64;  // per warp: up to 31 left over + 32 queued in one step
+
+struct BatchRun {  // a thread's run of hits for one graph of a batch
+  uint32_t g = 0xFFFFFFFFu;
+  unsigned long long hits = 0, lo = 0, hi = 0;  // graph g holds the vertices [lo, hi)
+  __device__ __forceinline__ void add(uint32_t u, unsigned long long here,
+                                      const unsigned long long* __restrict__ voff, uint32_t nb,
+                                      unsigned long long* __restrict__ gcount) {
+    if (u < lo || u >= hi) {  // another graph than the run's
+      if (hits) atomicAdd(&gcount[g], hits);
+      g = batch_graph_of(voff, 0, nb - 1, u);
+      lo = voff[g];
+      hi = voff[g + 1];
+      hits = 0;
+    }
+    hits += here;
+  }
+  __device__ __forceinline__ void flush(unsigned long long* __restrict__ gcount) {
+    if (hits) atomicAdd(&gcount[g], hits);
+  }
+};
+
+__device__ __forceinline__ void merge_small(uint2 e, const unsigned long long* __restrict__ row_ptr,
+                                            const uint32_t* __restrict__ col,
+                                            const int32_t* __restrict__ level,
+                                            const unsigned long long* __restrict__ voff,
+                                            uint32_t nb, unsigned long long* __restrict__ gcount,
+                                            Tally& tl, BatchRun& run) {
+  const uint32_t u = e.x, v = e.y;
+  const int32_t lu = level[u];
+  uint32_t here = 0;
+  block_merge(col, row_ptr[u], row_ptr[u + 1], row_ptr[v], row_ptr[v + 1], [&](uint32_t w) {
+    if (level[w] != lu) {
+      ++tl.c1;
+      ++here;
+    } else if (v < w) {
+      ++tl.c2c;
+      ++here;
+    }
+  });
+  if (nb && here) run.add(u, here, voff, nb, gcount);
+}
+
 template <bool kEmit>
 __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long* __restrict__ row_ptr,
                                                        const uint32_t* __restrict__ col,
+                                                       const uint32_t* __restrict__ erow,
                                                        const int32_t* __restrict__ level, uint32_t n,
                                                        unsigned long long nnz, uint32_t small_max,
                                                        uint2* __restrict__ cover,
@@ -198,32 +249,24 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                                                        uint32_t nb,
                                                        unsigned long long* __restrict__ gcount,
                                                        DevCounters* ctr, Emit em) {
-  __shared__ uint32_t s_lo, s_hi, s_g0, s_g1;
+  __shared__ uint2 s_q[kEmit ? 1 : kCoverBlock / kWarp][kEmit ? 1 : kSmallQueue];
   Tally tl;
-  // batch mode: counts of the inline merges go to their graph, one atomic per
-  // run of edges of the same graph seen by this thread
-  uint32_t run_g = 0xFFFFFFFFu;
-  unsigned long long run = 0;
+  // batch mode: the merges' hits go to their graph, one atomic per run of
+  // edges of the same graph seen by this thread
+  BatchRun run;
+  uint32_t qn = 0;  // small cover edges queued by this warp (warp-uniform)
+  uint2* const q = s_q[kEmit ? 0 : threadIdx.x / kWarp];
+  // each block takes tiles of consecutive entries; a thread's entries in a
+  // tile are kCoverBlock apart (coalesced), and their rows come from erow
   for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
        e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
     const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_lo = row_of(row_ptr, 0, n - 1, e0);
-      s_hi = row_of(row_ptr, s_lo, n - 1, e1 - 1);
-      if (nb) {
-        s_g0 = batch_graph_of(voff, 0, nb - 1, s_lo);
-        s_g1 = batch_graph_of(voff, s_g0, nb - 1, s_hi);
-      }
-    }
-    __syncthreads();
-    const uint32_t lo = s_lo, hi = s_hi;
     for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
       const unsigned long long j = b + threadIdx.x;
-      bool is_cover = false, is_large = false, is_medium = false;
+      bool is_cover = false, is_large = false, is_medium = false, is_small = false;
       uint2 ce = make_uint2(0, 0), le = make_uint2(0, 0);
       if (j < e1) {
-        const uint32_t u = row_of(row_ptr, lo, hi, j);
+        const uint32_t u = erow[j];
         const uint32_t v = col[j];
         if (check_failed(v >= n, ctr)) {
         } else if (v > u) {
@@ -234,8 +277,10 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
             const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
             const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
             const unsigned long long du = eu - bu, dv = ev - bv;
-            if (du <= small_max && dv <= small_max) {
-              // merge of N(u) and N(v) (blocked two-pointer merge)
+            if (!kEmit && du <= small_max && dv <= small_max) {
+              is_small = true;  // queued; merged by a lane of this warp (merge_small)
+            } else if (du <= small_max && dv <= small_max) {
+              // listing: merge of N(u) and N(v) by this thread, then again to write
               uint32_t here = 0;
               block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
                 if (level[w] != lu) {
@@ -266,15 +311,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
                   }
                 });
               }
-              if (nb && here) {
-                const uint32_t gid = s_g0 == s_g1 ? s_g0 : batch_graph_of(voff, s_g0, s_g1, u);
-                if (gid != run_g) {
-                  if (run) atomicAdd(&gcount[run_g], run);
-                  run_g = gid;
-                  run = 0;
-                }
-                run += here;
-              }
+
             } else if (du <= medium_max && dv <= medium_max) {
               is_medium = true;
             } else {
@@ -289,9 +326,27 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
       warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
       warp_append_pair(is_medium, ce, medium, &ctr->num_medium);
       warp_append_pair(is_large, le, large, &ctr->num_large);
+      if (!kEmit) {
+        const unsigned lane = lane_id();
+        const unsigned m = __ballot_sync(0xffffffffu, is_small);
+        if (is_small) q[qn + __popc(m & ((1u << lane) - 1u))] = ce;
+        qn += __popc(m);
+        if (qn >= kWarp) {  // every lane merges one queued edge
+          __syncwarp();
+          merge_small(q[lane], row_ptr, col, level, voff, nb, gcount, tl, run);
+          __syncwarp();
+          if (lane < qn - kWarp) q[lane] = q[kWarp + lane];
+          qn -= kWarp;
+          __syncwarp();
+        }
+      }
     }
   }
-  if (run) atomicAdd(&gcount[run_g], run);
+  if (!kEmit) {
+    __syncwarp();
+    if (lane_id() < qn) merge_small(q[lane_id()], row_ptr, col, level, voff, nb, gcount, tl, run);
+  }
+  if (nb) run.flush(gcount);
   flush_tally(tl, ctr);
 }
 
@@ -986,28 +1041,21 @@ __global__ void __launch_bounds__(kCoverBlock) k_forward_pairs(
 // the longer G1 row, ties larger id).  Hits are tallied as c1.
 __global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
     const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-    const int32_t* __restrict__ level, const uint32_t* __restrict__ lcol,
+    const uint32_t* __restrict__ erow, const int32_t* __restrict__ level,
+    const uint32_t* __restrict__ lcol,
     const unsigned long long* __restrict__ lsplit, uint32_t n, unsigned long long nnz,
     uint32_t small_max, uint2* __restrict__ cover, uint2* __restrict__ large,
     uint32_t* __restrict__ ocount, DevCounters* ctr) {
-  __shared__ uint32_t s_lo, s_hi;
   Tally tl;
   for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
        e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
     const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_lo = row_of(row_ptr, 0, n - 1, e0);
-      s_hi = row_of(row_ptr, s_lo, n - 1, e1 - 1);
-    }
-    __syncthreads();
-    const uint32_t lo = s_lo, hi = s_hi;
     for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
       const unsigned long long j = b + threadIdx.x;
       bool is_cover = false, is_large = false;
       uint2 ce = make_uint2(0, 0), le = make_uint2(0, 0);
       if (j < e1) {
-        const uint32_t u = row_of(row_ptr, lo, hi, j);
+        const uint32_t u = erow[j];
         const uint32_t v = col[j];
         if (v > u && level[v] == level[u]) {
           is_cover = true;
@@ -1038,10 +1086,26 @@ __global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
 
 // |S|: the horizontal edges {u, v}, u < v (one thread per adjacency entry).
 __global__ void __launch_bounds__(kCoverBlock) k_horizontal(
-    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-    const int32_t* __restrict__ level, uint32_t n, unsigned long long nnz, DevCounters* ctr) {
-  __shared__ uint32_t s_lo, s_hi;
+    const uint32_t* __restrict__ erow, const uint32_t* __restrict__ col,
+    const int32_t* __restrict__ level, unsigned long long nnz, DevCounters* ctr) {
   unsigned long long mine = 0;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t u = erow[j], v = col[j];
+    mine += v > u && level[v] == level[u];
+  }
+  mine = warp_sum(mine);
+  if (lane_id() == 0 && mine) atomicAdd(&ctr->num_cover, mine);
+}
+
+// erow[j] = the row of entry j, one thread per entry: each block takes a tile
+// of kCoverEntriesPerBlock consecutive entries, finds the rows the tile spans
+// (two searches of row_ptr by one thread) and every thread its entry's row
+// within them.  Runs once per graph, at creation.
+__global__ void __launch_bounds__(kCoverBlock) k_fill_rows(
+    const unsigned long long* __restrict__ row_ptr, uint32_t n, unsigned long long nnz,
+    uint32_t* __restrict__ erow) {
+  __shared__ uint32_t s_lo, s_hi;
   for (unsigned long long e0 = (unsigned long long)blockIdx.x * kCoverEntriesPerBlock; e0 < nnz;
        e0 += (unsigned long long)gridDim.x * kCoverEntriesPerBlock) {
     const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
@@ -1052,14 +1116,9 @@ __global__ void __launch_bounds__(kCoverBlock) k_horizontal(
     }
     __syncthreads();
     const uint32_t lo = s_lo, hi = s_hi;
-    for (unsigned long long j = e0 + threadIdx.x; j < e1; j += kCoverBlock) {
-      const uint32_t u = row_of(row_ptr, lo, hi, j);
-      const uint32_t v = col[j];
-      mine += v > u && level[v] == level[u];
-    }
+    for (unsigned long long j = e0 + threadIdx.x; j < e1; j += kCoverBlock)
+      erow[j] = row_of(row_ptr, lo, hi, j);
   }
-  mine = warp_sum(mine);
-  if (lane_id() == 0 && mine) atomicAdd(&ctr->num_cover, mine);
 }
 
 // Level-split rows of the whole graph: short rows by warps, long rows in tiles.
@@ -1172,6 +1231,14 @@ tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
   return need <= (size_t)optin ? TC_OK : TC_ERR_INVALID_ARG;
 }
 
+tc_status fill_entry_rows(tc_graph* g, cudaStream_t st) {
+  if (g->nnz == 0 || g->n == 0) return TC_OK;
+  k_fill_rows<<<grid_for(g->nnz, kCoverEntriesPerBlock, num_sms() * 16), kCoverBlock, 0, st>>>(
+      g->row_ptr, g->n, g->nnz, g->erow); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   const uint32_t n = g->n;
   const int sms = num_sms();
@@ -1183,7 +1250,7 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   const uint32_t small_max = g->params.small_max_degree;
   k_cover<false><<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
+      g->row_ptr, g->col, g->erow, g->level, n, g->nnz, small_max, g->cover, g->large, g->ocount,
       g->params.medium_max_degree > kMediumCap ? kMediumCap : g->params.medium_max_degree,
       g->medium, g->voff, g->batch_k, g->gcount, g->ctr, Emit{}); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
@@ -1277,7 +1344,7 @@ tc_status run_split_count(tc_graph* g, cudaStream_t st) {
   // T1: intersections of G1 rows over the edges of G0 (the cover edges)
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   k_g1_pairs<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, g->lcol, g->lsplit, n, g->nnz, g->params.small_max_degree,
+      g->row_ptr, g->col, g->erow, g->level, g->lcol, g->lsplit, n, g->nnz, g->params.small_max_degree,
       g->cover, g->large, g->ocount, g->ctr); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_CUDA_TRY(cudaEventRecord(g->ev[2], st));
@@ -1297,8 +1364,8 @@ tc_status run_count_horizontal(tc_graph* g, cudaStream_t st, unsigned long long*
   const int sms = num_sms();
   TC_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(DevCounters), st));
   if (g->nnz > 0) {
-    k_horizontal<<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-        g->row_ptr, g->col, g->level, g->n, g->nnz, g->ctr); TC_LAUNCHED();
+    k_horizontal<<<grid_for(g->nnz, kCoverBlock, sms * 16), kCoverBlock, 0, st>>>(
+        g->erow, g->col, g->level, g->nnz, g->ctr); TC_LAUNCHED();
     TC_CUDA_TRY(cudaGetLastError());
   }
   TC_CUDA_TRY(cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -1316,8 +1383,8 @@ tc_status run_cover_and_list(tc_graph* g, const EmitSink& sink, cudaStream_t st)
   const Emit em{sink.tri, sink.cap, &g->ctr->listed, sink.vcount, 0, 0};
   TC_CUDA_TRY(cudaMemsetAsync(g->ocount, 0, sizeof(uint32_t) * n, st));
   k_cover<true><<<grid_for(g->nnz, kCoverEntriesPerBlock, sms * 16), kCoverBlock, 0, st>>>(
-      g->row_ptr, g->col, g->level, n, g->nnz, g->params.small_max_degree, g->cover, g->large,
-      g->ocount, 0, g->medium, nullptr, 0, nullptr, g->ctr, em); TC_LAUNCHED();
+      g->row_ptr, g->col, g->erow, g->level, n, g->nnz, g->params.small_max_degree, g->cover,
+      g->large, g->ocount, 0, g->medium, nullptr, 0, nullptr, g->ctr, em); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   unsigned long long nlarge = 0;
   TC_TRY(scan_owners(g, st, &nlarge));

@@ -111,7 +111,7 @@ tc_status dalloc(const tc_graph* g, T** p, size_t count, cudaStream_t st) {
 
 void free_graph(tc_graph* g) {
   if (!g) return;
-  void* ptrs[] = {g->row_ptr, g->col,   g->level,  g->queue_a, g->queue_b, g->qoff,
+  void* ptrs[] = {g->row_ptr, g->col,   g->erow,   g->level,  g->queue_a, g->queue_b, g->qoff,
                   g->ooff,    g->ioff,  g->parent, g->fdeg,    g->ocount,  g->ofill,
                   g->cover,   g->large, g->ostream, g->item_owner, g->ctr, g->scan.sums,
                   g->lcol,    g->lsplit, g->tile_row, g->tile_cnt, g->medium, g->obeg,
@@ -153,7 +153,8 @@ tc_status alloc_count_state(tc_graph* g, cudaStream_t st) {
   TC_TRY(dalloc(g, &g->tile_cnt, g->tile_cap, st));
   g->scan.capacity = scan_scratch_entries(n + 1);
   TC_TRY(dalloc(g, &g->scan.sums, g->scan.capacity, st));
-  return TC_OK;
+  TC_TRY(dalloc(g, &g->erow, g->nnz, st));
+  return fill_entry_rows(g, st);
 }
 
 void params_default(tc_params* p) {

@@ -71,6 +71,7 @@ struct tc_graph {
   uint32_t maxdeg_vertex = 0;
   unsigned long long* row_ptr = nullptr;  // [n+1]
   uint32_t* col = nullptr;                // [nnz]
+  uint32_t* erow = nullptr;               // [nnz] row of each entry (the CSR's rows as COO)
 
   // per-count state, sized at creation so a count allocates nothing
   int32_t* level = nullptr;      // [n]
@@ -213,6 +214,9 @@ __device__ __forceinline__ uint32_t batch_graph_of(const unsigned long long* off
   return lo;
 }
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
+// g->erow[j] = the row of adjacency entry j (after the CSR is built; once per
+// graph: the per-count entry loops read it instead of searching row_ptr).
+tc_status fill_entry_rows(tc_graph* g, cudaStream_t st);
 // TC_OK if owner-hash blocks of `hash_block` threads with chunks of `chunk`
 // entries fit the device's shared memory per block, else TC_ERR_INVALID_ARG.
 tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block);

@@ -40,11 +40,12 @@ import paper_2403_02997_gb300 as tc
 def footprint_bytes(n: int, draws: int) -> int:
     """Device bytes one request may hold.
 
-    This counts the graph handle (CSR + per-count state, with m <= draws undirected edges), its
-    share of the batch union (a second copy of the same), and the transient sort buffers of the
-    build (two arrays of 2·draws 8-byte keys plus the staged edge list).
+    This counts the graph handle (CSR, its row array, and the per-count state, with m <= draws
+    undirected edges), its share of the batch union (a second copy of the same), and the
+    transient sort buffers of the build (two arrays of 2·draws 8-byte keys plus the staged edge
+    list).
     """
-    per_graph = 8 * (n + 1) + 4 * (2 * draws + 8) + 68 * n + 36 * draws
+    per_graph = 8 * (n + 1) + 4 * (2 * draws + 8) + 68 * n + 44 * draws
     transient = 32 * draws + 8 * draws
     return 2 * per_graph + transient + (1 << 16)
 

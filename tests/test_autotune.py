@@ -53,3 +53,37 @@ def test_a_changed_count_is_an_error():
     t = FakeTarget(cheat={"hash_chunk": 4096})
     with pytest.raises(RuntimeError):
         autotune.tune(t, 0, trials=1)
+
+
+class FakeGraph:
+    """count(): the cover-edge count, count_forward(): the forward count, with given times."""
+
+    def __init__(self, ms_cetc, ms_fwd, num_cover=300, m=1000, tri=7, fwd_tri=7):
+        self.ms_cetc, self.ms_fwd, self.num_cover, self.m = ms_cetc, ms_fwd, num_cover, m
+        self.tri, self.fwd_tri, self.last = tri, fwd_tri, 0.0
+
+    def count(self, root):
+        self.last = self.ms_cetc
+        return self.tri
+
+    def count_forward(self):
+        self.last = self.ms_fwd
+        return self.fwd_tri
+
+    def stats(self):
+        return {"ms_total": self.last, "num_cover": self.num_cover}
+
+
+def test_fe_threshold_follows_the_faster_count(tmp_path):
+    fast_fwd = autotune.learn_fe_threshold(FakeGraph(10.0, 6.0), 0, trials=1)
+    assert fast_fwd["forward_faster"] and fast_fwd["threshold"] < 0.3      # c = 0.3 switches
+    slow_fwd = autotune.learn_fe_threshold(FakeGraph(6.0, 10.0), 0, trials=1)
+    assert not slow_fwd["forward_faster"] and slow_fwd["threshold"] > 0.3  # c = 0.3 stays
+    path = str(tmp_path / "cache.json")
+    autotune.store_fe("rmat:n24", fast_fwd, path)
+    autotune.store("rmat:n24", {"params": {"hash_chunk": 4096}, "ms": 1.0, "default_ms": 2.0}, path)
+    assert autotune.lookup_fe("rmat:n24", path) == fast_fwd["threshold"]   # both kept
+    assert autotune.lookup("rmat:n24", path) == {"hash_chunk": 4096}
+    assert autotune.lookup_fe("missing", path) is None
+    with pytest.raises(RuntimeError):                                    # counts must agree
+        autotune.learn_fe_threshold(FakeGraph(10.0, 6.0, fwd_tri=8), 0, trials=1)

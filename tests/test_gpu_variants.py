@@ -214,3 +214,21 @@ def test_triangle_listing(gi, pname):
         assert g.count(root) == T  # the handle counts as before
     finally:
         g.close()
+
+
+def test_fe_with_learned_threshold():
+    """The autotuner's CETC-Seq-FE threshold sends the graph down the branch that was faster on
+    it, and that branch's count is the oracle's."""
+    from paper_2403_02997_gb300 import autotune
+    n = 1 << 14
+    s, d = gen.rmat_edges(14, 16, 21)
+    rp, col = oracle.build_csr(n, s, d)
+    root = oracle.max_degree_root(rp)
+    want = oracle.forward(rp, col)
+    g = tc.Graph(s, d, n)
+    try:
+        fe = autotune.learn_fe_threshold(g, root, trials=2)
+        T, used = g.count_fe(root, fe["threshold"])
+        assert T == want and bool(used) == fe["forward_faster"]
+    finally:
+        g.close()
