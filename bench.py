@@ -37,7 +37,8 @@ from paper_2403_02997_gb300 import gen  # noqa: E402
 
 WORKLOADS = {"rmat24": gen.RMAT_24, "er1024": gen.ER_1024, "mesh4096": gen.MESH_4096,
              # smaller cases of the same family, for profiling captures
-             "rmat21": gen.rmat_spec(21, 16, 2), "rmat23": gen.rmat_spec(23, 16, 2),
+             "rmat21": gen.rmat_spec(21, 16, 2), "rmat22": gen.rmat_spec(22, 16, 2),
+             "rmat23": gen.rmat_spec(23, 16, 2),
              "rmat16": gen.rmat_spec(16, 16, 2)}
 METRIC = "input edges/s (exact triangle count, tc_count on device-resident CSR)"
 L2_BYTES = 129 * 2**20
@@ -274,8 +275,9 @@ class OracleSampler:
     * the oracle BFS over the whole graph with its restarts (one thread);
     * its cover-edge scan: the CETC-Seq edge loop with the intersections
       sampled out (orc_cetc with a stride beyond |S|; one thread);
-    * the per-edge intersections of a seeded uniform sample of S, twice:
-      ``seq``, the literal CETC-Seq edge loop on one thread (orc_cetc_edges),
+    * the per-edge intersections of a seeded sample of S (random runs of 512
+      consecutive cover edges, so the sample keeps the full loop's row locality),
+      twice: ``seq``, the literal CETC-Seq edge loop on one thread (orc_cetc_edges),
       and ``omp``, Algorithm CETC-SM's parallel edge loop on all host threads
       (orc_cetc_sm_edges).  Each sample grows geometrically until it has used
       about its time budget.
@@ -297,21 +299,32 @@ class OracleSampler:
         self.cores = int(oracle.num_threads())
         self.num_cover = None
 
-    def _sample(self, fn, lv, cov, budget):
-        """Grows a uniform sample of S until about `budget` seconds; (edges, seconds)."""
+    def _sample(self, fn, lv, cov, budget, cores):
+        """Grows a uniform sample of S until about `budget` seconds.
+
+        Returns (edges, seconds) of the batches that kept every thread busy (at least 1024 edges
+        per thread), or of all batches when none did: the first, small batches mostly time the
+        threads' start-up, which would bias the per-edge time upwards.
+        """
         S = self.num_cover
         done, spent, k = 0, 0.0, 64
+        batches = []
+        run = 512  # consecutive cover edges per pick: the full loop's row locality is kept
         while S and spent < budget and done < 4 * S:
             k = min(k, S)
-            idx = self.rng.integers(0, S, size=k)
+            starts = self.rng.integers(0, max(S - run, 0) + 1, size=max(1, k // run))
+            idx = (starts[:, None] + np.arange(min(run, S))[None, :]).ravel()[:max(k, 1)]
+            k = idx.size
             us, vs = cov["cover_u"][idx], cov["cover_v"][idx]
             t = time.perf_counter()
             fn(self.rp, self.col, lv, us, vs)
             dt = time.perf_counter() - t
+            batches.append((k, dt))
             spent += dt
             done += k
             k = int(k * min(4.0, max(1.5, (budget - spent) / max(dt, 1e-6))))
-        return done, spent
+        full = [(k_, t_) for k_, t_ in batches if k_ >= 1024 * cores] or batches
+        return sum(k_ for k_, _ in full), sum(t_ for _, t_ in full)
 
     def step(self) -> dict:
         t0 = time.perf_counter()
@@ -323,7 +336,8 @@ class OracleSampler:
         self.num_cover = S = cov["num_cover"]
         out = {"edges": self.m, "num_cover": S, "bfs_s": t_bfs, "scan_s": t_scan}
         for name, fn, share in (("seq", self.o.cetc_edges, 0.4), ("omp", self.o.cetc_sm_edges, 0.6)):
-            done, spent = self._sample(fn, lv, cov, share * self.target_s)
+            done, spent = self._sample(fn, lv, cov, share * self.target_s,
+                                       1 if name == "seq" else self.cores)
             est = t_bfs + t_scan + (spent / done) * S if done else t_bfs + t_scan
             out[name] = {"sampled_edges": done, "sample_s": spent, "est_full_seconds": est,
                          "cores": 1 if name == "seq" else self.cores,
@@ -333,7 +347,8 @@ class OracleSampler:
 
     def describe(self, r) -> str:
         return (f"oracle BFS over the whole graph + full cover-edge scan (1 thread each), then the "
-                f"per-edge intersections of seeded uniform samples of S (|S| = {r['num_cover']}): "
+                f"per-edge intersections of seeded samples of S (random runs of 512 consecutive "
+                f"cover edges; |S| = {r['num_cover']}): "
                 f"{r['seq']['sampled_edges']} edges by the literal CETC-Seq loop on 1 thread, "
                 f"{r['omp']['sampled_edges']} by the CETC-SM parallel loop on {self.cores} "
                 f"threads; full-graph time = bfs + scan + sample seconds per edge x |S|")
@@ -716,6 +731,22 @@ def measure_batched(args, world, rank, local) -> dict:
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     graphs_total = sum_over_ranks(float(len(gs)) * args.steps, world)
     value = graphs_total / (ms / 1e3)
+    # the fixed cost of a batch: the 64 smallest graphs counted as one batch
+    small_ix = sorted(range(len(gs)), key=lambda i: gs[i].m)[:64]
+    sb = tc.Batch([gs[i] for i in small_ix], stream=stream)
+    if tuned:
+        sb.set_params(**tuned)
+    small_roots = [roots[i] for i in small_ix]
+    for _ in range(3):
+        sb.count(small_roots, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        sb.count(small_roots, stream=stream)
+    small_ms = (time.perf_counter() - t0) / 20 * 1e3
+    small_launches = sb.stats()["launches"]
+    small_edges = int(sum(gs[i].m for i in small_ix))
+    sb.close()
     # one tc_count per graph, same GPU, same graphs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -767,6 +798,9 @@ def measure_batched(args, world, rank, local) -> dict:
                                   "what": "tc_graph_create per graph + tc_count_many"},
         "gpu_launches": st["launches"] * args.steps,
         "launches_per_batch": st["launches"],
+        "small_batch": {"graphs": len(small_ix), "edges": small_edges, "ms_per_batch": small_ms,
+                        "launches": small_launches,
+                        "what": "the 64 smallest graphs as one batch: the fixed cost of a batch"},
         "clocks": clk,
     }
 

@@ -184,13 +184,12 @@ struct Emit {
   }
 };
 
-// The small bin (both degrees <= small_max), compacted: k_cover queues these
-// cover edges per warp (ballot ranks into shared memory) and, once 32 are
-// queued, every lane merges one of them (block_merge).  Without the queue
-// only the lanes whose entry happened to be a small cover edge -- about a
-// quarter of them -- would merge while the rest of the warp waited.  A
-// common neighbour w counts as in Algorithm CETC-Seq: c1 when L(w) != L(u),
-// c2' when L(w) == L(u) and v < w.  In batch mode the hits go to u's graph.
+// Cover edges, compacted: k_cover queues the cover edges its lanes find (ballot
+// ranks into a per-warp shared-memory queue) and, once 32 are queued, every
+// lane bins one of them (bin_cover: its rows' offsets, then the small-bin
+// merge or an append).  Without the queue only the lanes whose entry happened
+// to be a cover edge -- about a quarter of them -- would do that work while
+// the rest of the warp waited.  In batch mode the hits go to u's graph.
 constexpr int kSmallQueue = 64;  // per warp: up to 31 left over + 32 queued in one step
 
 struct BatchRun {  // a thread's run of hits for one graph of a batch
@@ -213,25 +212,55 @@ struct BatchRun {  // a thread's run of hits for one graph of a batch
   }
 };
 
-__device__ __forceinline__ void merge_small(uint2 e, const unsigned long long* __restrict__ row_ptr,
-                                            const uint32_t* __restrict__ col,
-                                            const int32_t* __restrict__ level,
-                                            const unsigned long long* __restrict__ voff,
-                                            uint32_t nb, unsigned long long* __restrict__ gcount,
-                                            Tally& tl, BatchRun& run) {
-  const uint32_t u = e.x, v = e.y;
-  const int32_t lu = level[u];
-  uint32_t here = 0;
-  block_merge(col, row_ptr[u], row_ptr[u + 1], row_ptr[v], row_ptr[v + 1], [&](uint32_t w) {
-    if (level[w] != lu) {
-      ++tl.c1;
-      ++here;
-    } else if (v < w) {
-      ++tl.c2c;
-      ++here;
+// Bins one queued cover edge {u, v} and counts it if it is in the small bin;
+// called by every lane of the warp (the appends are warp-collective), with
+// `valid` false on lanes that hold no edge.  Small bin (both degrees <=
+// small_max): the blocked merge of N(u) and N(v); a common neighbour w counts
+// as in Algorithm CETC-Seq, c1 when L(w) != L(u), c2' when L(w) == L(u) and
+// v < w.  Medium bin: appended for k_warp_merge.  Otherwise: appended for the
+// owner-hash pass as (owner, streamer), the owner the endpoint of larger
+// degree (ties: larger id), and counted in ocount[owner].
+__device__ __forceinline__ void bin_cover(bool valid, uint2 e,
+                                          const unsigned long long* __restrict__ row_ptr,
+                                          const uint32_t* __restrict__ col,
+                                          const int32_t* __restrict__ level, uint32_t small_max,
+                                          uint32_t medium_max, uint32_t* __restrict__ ocount,
+                                          uint2* __restrict__ medium, uint2* __restrict__ large,
+                                          DevCounters* ctr,
+                                          const unsigned long long* __restrict__ voff,
+                                          uint32_t nb, unsigned long long* __restrict__ gcount,
+                                          Tally& tl, BatchRun& run) {
+  bool is_medium = false, is_large = false;
+  uint2 le = make_uint2(0, 0);
+  if (valid) {
+    const uint32_t u = e.x, v = e.y;
+    const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
+    const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
+    const int32_t lu = level[u];
+    const unsigned long long du = eu - bu, dv = ev - bv;
+    if (du <= small_max && dv <= small_max) {
+      uint32_t here = 0;
+      block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
+        if (level[w] != lu) {
+          ++tl.c1;
+          ++here;
+        } else if (v < w) {
+          ++tl.c2c;
+          ++here;
+        }
+      });
+      if (nb && here) run.add(u, here, voff, nb, gcount);
+    } else if (du <= medium_max && dv <= medium_max) {
+      is_medium = true;
+    } else {
+      is_large = true;
+      const bool v_owns = dv > du || (dv == du && v > u);
+      le = v_owns ? make_uint2(v, u) : make_uint2(u, v);
+      atomicAdd(&ocount[le.x], 1u);
     }
-  });
-  if (nb && here) run.add(u, here, voff, nb, gcount);
+  }
+  warp_append_pair(is_medium, e, medium, &ctr->num_medium);
+  warp_append_pair(is_large, le, large, &ctr->num_large);
 }
 
 template <bool kEmit>
@@ -254,7 +283,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
   // batch mode: the merges' hits go to their graph, one atomic per run of
   // edges of the same graph seen by this thread
   BatchRun run;
-  uint32_t qn = 0;  // small cover edges queued by this warp (warp-uniform)
+  uint32_t qn = 0;  // cover edges queued by this warp (warp-uniform)
   uint2* const q = s_q[kEmit ? 0 : threadIdx.x / kWarp];
   // each block takes tiles of consecutive entries; a thread's entries in a
   // tile are kCoverBlock apart (coalesced), and their rows come from erow
@@ -263,7 +292,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
     const unsigned long long e1 = min(nnz, e0 + kCoverEntriesPerBlock);
     for (unsigned long long b = e0; b < e1; b += kCoverBlock) {
       const unsigned long long j = b + threadIdx.x;
-      bool is_cover = false, is_large = false, is_medium = false, is_small = false;
+      bool is_cover = false, is_large = false, is_medium = false;
       uint2 ce = make_uint2(0, 0), le = make_uint2(0, 0);
       if (j < e1) {
         const uint32_t u = erow[j];
@@ -274,66 +303,67 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
           if (level[v] == lu) {
             is_cover = true;
             ce = make_uint2(u, v);
-            const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
-            const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
-            const unsigned long long du = eu - bu, dv = ev - bv;
-            if (!kEmit && du <= small_max && dv <= small_max) {
-              is_small = true;  // queued; merged by a lane of this warp (merge_small)
-            } else if (du <= small_max && dv <= small_max) {
-              // listing: merge of N(u) and N(v) by this thread, then again to write
-              uint32_t here = 0;
-              block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
-                if (level[w] != lu) {
-                  ++tl.c1;
-                  ++here;
-                } else if (v < w) {
-                  ++tl.c2c;
-                  ++here;
-                }
-              });
-              if (kEmit && here) {
-                // the same merge again, writing this edge's triangles to the
-                // slots reserved for them
-                unsigned long long pos = em.tri ? atomicAdd(em.cursor, (unsigned long long)here) : 0;
-                if (em.vcount) {
-                  atomicAdd(&em.vcount[u], (unsigned long long)here);
-                  atomicAdd(&em.vcount[v], (unsigned long long)here);
-                }
+            if (kEmit) {  // listing: binned and merged by this thread
+              const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
+              const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
+              const unsigned long long du = eu - bu, dv = ev - bv;
+              if (du <= small_max && dv <= small_max) {
+                // merge of N(u) and N(v), then again to write its triangles to
+                // the slots reserved for them
+                uint32_t here = 0;
                 block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
-                  if (level[w] != lu || v < w) {
-                    if (em.tri && pos < em.cap) {
-                      em.tri[3 * pos] = u;
-                      em.tri[3 * pos + 1] = v;
-                      em.tri[3 * pos + 2] = w;
-                    }
-                    ++pos;
-                    if (em.vcount) atomicAdd(&em.vcount[w], 1ull);
+                  if (level[w] != lu) {
+                    ++tl.c1;
+                    ++here;
+                  } else if (v < w) {
+                    ++tl.c2c;
+                    ++here;
                   }
                 });
+                if (here) {
+                  unsigned long long pos =
+                      em.tri ? atomicAdd(em.cursor, (unsigned long long)here) : 0;
+                  if (em.vcount) {
+                    atomicAdd(&em.vcount[u], (unsigned long long)here);
+                    atomicAdd(&em.vcount[v], (unsigned long long)here);
+                  }
+                  block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
+                    if (level[w] != lu || v < w) {
+                      if (em.tri && pos < em.cap) {
+                        em.tri[3 * pos] = u;
+                        em.tri[3 * pos + 1] = v;
+                        em.tri[3 * pos + 2] = w;
+                      }
+                      ++pos;
+                      if (em.vcount) atomicAdd(&em.vcount[w], 1ull);
+                    }
+                  });
+                }
+              } else if (du <= medium_max && dv <= medium_max) {
+                is_medium = true;
+              } else {
+                is_large = true;
+                const bool v_owns = dv > du || (dv == du && v > u);
+                le = v_owns ? make_uint2(v, u) : make_uint2(u, v);
+                atomicAdd(&ocount[le.x], 1u);
               }
-
-            } else if (du <= medium_max && dv <= medium_max) {
-              is_medium = true;
-            } else {
-              is_large = true;
-              const bool v_owns = dv > du || (dv == du && v > u);
-              le = v_owns ? make_uint2(v, u) : make_uint2(u, v);
-              atomicAdd(&ocount[le.x], 1u);
             }
           }
         }
       }
       warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
-      warp_append_pair(is_medium, ce, medium, &ctr->num_medium);
-      warp_append_pair(is_large, le, large, &ctr->num_large);
-      if (!kEmit) {
+      if (kEmit) {
+        warp_append_pair(is_medium, ce, medium, &ctr->num_medium);
+        warp_append_pair(is_large, le, large, &ctr->num_large);
+      } else {
         const unsigned lane = lane_id();
-        const unsigned m = __ballot_sync(0xffffffffu, is_small);
-        if (is_small) q[qn + __popc(m & ((1u << lane) - 1u))] = ce;
+        const unsigned m = __ballot_sync(0xffffffffu, is_cover);
+        if (is_cover) q[qn + __popc(m & ((1u << lane) - 1u))] = ce;
         qn += __popc(m);
-        if (qn >= kWarp) {  // every lane merges one queued edge
+        if (qn >= kWarp) {  // every lane bins one queued cover edge
           __syncwarp();
-          merge_small(q[lane], row_ptr, col, level, voff, nb, gcount, tl, run);
+          bin_cover(true, q[lane], row_ptr, col, level, small_max, medium_max, ocount, medium,
+                    large, ctr, voff, nb, gcount, tl, run);
           __syncwarp();
           if (lane < qn - kWarp) q[lane] = q[kWarp + lane];
           qn -= kWarp;
@@ -344,7 +374,9 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
   }
   if (!kEmit) {
     __syncwarp();
-    if (lane_id() < qn) merge_small(q[lane_id()], row_ptr, col, level, voff, nb, gcount, tl, run);
+    const unsigned lane = lane_id();
+    bin_cover(lane < qn, lane < qn ? q[lane] : make_uint2(0, 0), row_ptr, col, level, small_max,
+              medium_max, ocount, medium, large, ctr, voff, nb, gcount, tl, run);
   }
   if (nb) run.flush(gcount);
   flush_tally(tl, ctr);
