@@ -252,7 +252,10 @@ typedef struct tc_params {
                                   longer row staged in shared memory, the shorter searched in it */
   uint32_t hash_block;       /* threads per owner-hash block: 512 (default) or 1024 (one block per
                                 SM; allows hash_chunk 16384 with the SM's full warp count) */
-  uint32_t reserved[1];
+  uint32_t cluster_bfs;      /* 1 (default, with persistent_bfs): runs of frontiers of at most 4096
+                                vertices of degree <= 8 go to a search in one cluster of 8 blocks
+                                (hardware cluster barrier between levels); 0: to the persistent
+                                kernel */
 } tc_params;
 
 tc_status tc_params_default(tc_params* p);

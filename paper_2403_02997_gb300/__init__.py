@@ -50,7 +50,7 @@ class tc_params(ctypes.Structure):
                 ("bfs_beta", ctypes.c_uint32), ("sorted_lookup", ctypes.c_uint32),
                 ("persistent_bfs", ctypes.c_uint32), ("barrier_timeout_ms", ctypes.c_uint32),
                 ("test_barrier_skip", ctypes.c_uint32), ("medium_max_degree", ctypes.c_uint32),
-                ("hash_block", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("hash_block", ctypes.c_uint32), ("cluster_bfs", ctypes.c_uint32)]
 
 
 _lib = None
@@ -249,7 +249,7 @@ def tc_max_degree_vertex(handle: int) -> int:
 def tc_params_default() -> dict:
     p = tc_params()
     _check(load_library().tc_params_default(ctypes.byref(p)), "tc_params_default")
-    return {name: getattr(p, name) for name, _ in tc_params._fields_ if name != "reserved"}
+    return {name: getattr(p, name) for name, _ in tc_params._fields_}
 
 
 def tc_set_params(handle: int, **kw) -> None:

@@ -25,6 +25,8 @@
 //   vertex the ascending restart loop starts from.  One multi-source BFS from
 //   all those roots (level 0) then gives every level at once; components do not
 //   interact, so the levels equal those of the sequential restarts.
+#include <cooperative_groups.h>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -286,6 +288,128 @@ __global__ void __launch_bounds__(kPersistBlock) k_bfs_persistent(
   }
 }
 
+// ---- cluster search for small, low-degree frontiers -----------------------
+//
+// Long, thin graphs (meshes, road networks) run thousands of levels whose
+// frontiers hold a few thousand low-degree vertices; a level's cost is then
+// the latency of its chain of dependent memory operations (queue entry, row
+// offsets, neighbour, the claiming CAS, the append).
+// k_bfs_cluster keeps that chain short: a group of kClusterGroup lanes takes a
+// frontier vertex and each lane one of its edges, and each group takes
+// kClusterPer vertices with their loads issued together, so a level is about
+// five dependent steps however its edges fall.  It runs in one thread-block
+// cluster of kClusterCtas blocks (one per SM): a level ends at the hardware
+// cluster barrier, and the next frontier's length is counted in block 0's
+// shared memory through distributed-shared-memory atomics (one per warp and
+// step, ballot ranks).  Every block reads the same counters after the
+// barrier, so all take the same exit: the next frontier empty, above
+// kClusterMaxVerts, or the level just expanded had a vertex of degree above
+// kClusterGroup (expanded anyway, in further steps).  There is no spin-wait,
+// hence no timeout path.  Queues written by other blocks are read with
+// __ldcg (L2), never through a stale L1 line.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 1024;
+constexpr uint32_t kClusterGroup = 8;
+constexpr uint32_t kClusterPer = 4;
+constexpr uint32_t kClusterGroups = (uint32_t)kClusterCtas * kClusterThreads / kClusterGroup;
+constexpr unsigned long long kClusterMaxVerts =
+    (unsigned long long)kClusterGroups * kClusterPer;  // 4096
+constexpr unsigned int kClusterMaxDeg = kClusterGroup;
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+    k_bfs_cluster(const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                  int32_t* level, uint32_t* q0, uint32_t* q1, uint32_t qlen0, int32_t lvl0,
+                  DevCounters* c) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  // next-frontier counters of block 0 in three slots: level `it` reads slot
+  // it%3, appends to slot (it+1)%3, and block 0 clears slot (it+2)%3, which
+  // every block read before the barrier that ended the previous level
+  __shared__ uint32_t s_len[3];
+  __shared__ int s_big[3];
+  const unsigned rank = cluster.block_rank(), lane = lane_id();
+  uint32_t* len0 = cluster.map_shared_rank(s_len, 0);
+  int* big0 = cluster.map_shared_rank(s_big, 0);
+  if (rank == 0 && threadIdx.x == 0) {
+    s_len[0] = qlen0;
+    s_len[1] = s_len[2] = 0;
+    s_big[0] = s_big[1] = s_big[2] = 0;
+  }
+  cluster.sync();
+  const uint32_t grp = (rank * kClusterThreads + threadIdx.x) / kClusterGroup;
+  const uint32_t gl = lane % kClusterGroup;
+  int32_t lvl = lvl0;
+  for (unsigned it = 0;; ++it) {
+    const unsigned cur = it % 3, nxt = (it + 1) % 3, old = (it + 2) % 3;
+    const uint32_t* q = (it & 1) ? q1 : q0;
+    uint32_t* nq = (it & 1) ? q0 : q1;
+    const uint32_t qlen = len0[cur];
+    if (rank == 0 && threadIdx.x == 0) {
+      s_len[old] = 0;
+      s_big[old] = 0;
+    }
+    uint32_t u[kClusterPer];
+    unsigned long long b[kClusterPer], e[kClusterPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kClusterPer; ++k) {
+      const uint32_t i = grp + k * kClusterGroups;
+      u[k] = i < qlen ? __ldcg(q + i) : kNoLevel;
+    }
+    unsigned long long dmax = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kClusterPer; ++k) {
+      b[k] = e[k] = 0;
+      if (u[k] != kNoLevel) {
+        b[k] = row_ptr[u[k]];
+        e[k] = row_ptr[u[k] + 1];
+      }
+      dmax = max(dmax, e[k] - b[k]);
+    }
+    if (dmax > kClusterMaxDeg && gl == 0) big0[nxt] = 1;
+    // steps of kClusterGroup edges (one for every vertex of degree <= kClusterGroup)
+    const unsigned steps = __reduce_max_sync(
+        0xffffffffu, (unsigned)((dmax + kClusterGroup - 1) / kClusterGroup));
+    for (unsigned t = 0; t < steps; ++t) {
+      uint32_t w[kClusterPer];
+      bool take[kClusterPer];
+#pragma unroll
+      for (uint32_t k = 0; k < kClusterPer; ++k) {
+        const unsigned long long j = b[k] + (unsigned long long)t * kClusterGroup + gl;
+        w[k] = j < e[k] ? col[j] : kNoLevel;
+      }
+      // the claiming CAS without a level read first: it returns the old level,
+      // so a visited neighbour costs one atomic instead of a load on the chain
+#pragma unroll
+      for (uint32_t k = 0; k < kClusterPer; ++k)
+        take[k] = w[k] != kNoLevel && atomicCAS(&level[w[k]], -1, lvl + 1) == -1;
+#pragma unroll
+      for (uint32_t k = 0; k < kClusterPer; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, take[k]);
+        if (m) {
+          const unsigned leader = __ffs(m) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(&len0[nxt], (uint32_t)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (take[k]) nq[base + __popc(m & ((1u << lane) - 1u))] = w[k];
+        }
+      }
+    }
+    cluster.sync();
+    const uint32_t nlen = len0[nxt];
+    const bool big = big0[nxt] != 0;
+    ++lvl;
+    if (nlen == 0 || nlen > kClusterMaxVerts || big) {
+      if (rank == 0 && threadIdx.x == 0) {
+        c->p_level = (unsigned)lvl;
+        c->plen[0] = nlen;
+        c->p_buf = (it + 1) & 1;
+      }
+      cluster.sync();  // block 0's counters stay alive until every block has read them
+      return;
+    }
+  }
+}
+
 // ---- restart components -------------------------------------------------
 
 __global__ void k_cc_init(uint32_t* parent, uint32_t n) {
@@ -392,6 +516,21 @@ tc_status run_persistent(tc_graph* g, uint32_t* q, uint32_t* nq, uint64_t qlen, 
   return TC_OK;
 }
 
+// One k_bfs_cluster run from the frontier q (qlen <= kClusterMaxVerts vertices
+// at level lvl); results as run_persistent.
+tc_status run_cluster(tc_graph* g, uint32_t* q, uint32_t* nq, uint64_t qlen, int32_t lvl,
+                      cudaStream_t st, int32_t* next_lvl, uint64_t* next_len, bool* next_in_b) {
+  k_bfs_cluster<<<kClusterCtas, kClusterThreads, 0, st>>>(g->row_ptr, g->col, g->level, q, nq,
+                                                          (uint32_t)qlen, lvl, g->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  TC_TRY(read_counters(g, st));
+  const DevCounters& h = *g->ctr_host;
+  *next_lvl = (int32_t)h.p_level;
+  *next_len = h.plen[0];
+  *next_in_b = h.p_buf == 1;
+  return TC_OK;
+}
+
 // Level-synchronous search from the vertices already in queue_a (qlen of them,
 // all at level 0).  Returns the number of levels (1 + deepest level).
 tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* levels_out) {
@@ -421,12 +560,18 @@ tc_status level_loop(tc_graph* g, uint64_t qlen, cudaStream_t st, uint32_t* leve
       TC_CUDA_TRY(cudaStreamSynchronize(st));
       fedges = g->ctr_host->scan_total;
       if ((long double)fedges * alpha > unexplored && qlen > 1) bottom_up = true;
-      if (!bottom_up && g->params.persistent_bfs && qlen <= kPersistMaxVerts &&
-          fedges <= kPersistMaxEdges && fedges > 0 && g->ctr_host->fmaxdeg <= kPersistMaxDeg) {
+      const bool in_cluster = g->params.cluster_bfs && qlen <= kClusterMaxVerts &&
+                              g->ctr_host->fmaxdeg <= kClusterMaxDeg;
+      if (!bottom_up && g->params.persistent_bfs && fedges > 0 &&
+          (in_cluster || (qlen <= kPersistMaxVerts && fedges <= kPersistMaxEdges &&
+                          g->ctr_host->fmaxdeg <= kPersistMaxDeg))) {
         int32_t next_lvl = lvl;
         uint64_t next_len = 0;
         bool next_in_b = false;
-        TC_TRY(run_persistent(g, q, nq, qlen, lvl, st, &next_lvl, &next_len, &next_in_b));
+        if (in_cluster)
+          TC_TRY(run_cluster(g, q, nq, qlen, lvl, st, &next_lvl, &next_len, &next_in_b));
+        else
+          TC_TRY(run_persistent(g, q, nq, qlen, lvl, st, &next_lvl, &next_len, &next_in_b));
         g->stats.bfs_steps += (uint32_t)(next_lvl - lvl);
         unexplored -= (long double)fedges;  // the first step's edges; later ones are small
         prev_frontier = next_len;

@@ -167,6 +167,7 @@ void params_default(tc_params* p) {
   p->persistent_bfs = 1;
   p->barrier_timeout_ms = 2000;
   p->hash_block = 512;
+  p->cluster_bfs = 1;
 }
 
 namespace {
@@ -204,6 +205,7 @@ tc_status tc_set_params(tc_graph* g, const tc_params* p) {
     return TC_ERR_INVALID_ARG;
   if (p->barrier_timeout_ms == 0 || p->barrier_timeout_ms > 600000) return TC_ERR_INVALID_ARG;
   if (p->medium_max_degree > 1024) return TC_ERR_INVALID_ARG;
+  if (p->cluster_bfs > 1) return TC_ERR_INVALID_ARG;
   TC_TRY(owner_hash_fits(c, p->hash_block));
   g->params = *p;
   return TC_OK;

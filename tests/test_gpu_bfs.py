@@ -94,7 +94,8 @@ def test_barrier_timeout_is_reported_and_handle_survives():
     g = tc.Graph(s, d, n)
     try:
         good = g.count(0)
-        g.set_params(test_barrier_skip=1, barrier_timeout_ms=50)
+        # the persistent kernel (not the cluster search) takes the mesh's frontiers
+        g.set_params(test_barrier_skip=1, barrier_timeout_ms=50, cluster_bfs=0)
         t0 = time.time()
         with pytest.raises(tc.TCError) as ei:
             g.count(0)
