@@ -746,7 +746,20 @@ def measure_batched(args, world, rank, local) -> dict:
     small_ms = (time.perf_counter() - t0) / 20 * 1e3
     small_launches = sb.stats()["launches"]
     small_edges = int(sum(gs[i].m for i in small_ix))
+    # the same small batch and the whole batch in one persistent launch (one graph per block)
+    assert sb.count_persistent(small_roots, stream=stream) == sb.count(small_roots, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        sb.count_persistent(small_roots, stream=stream)
+    small_persist_ms = (time.perf_counter() - t0) / 20 * 1e3
     sb.close()
+    assert b.count_persistent(roots, stream=stream) == counts
+    persist_ms = []
+    for _ in range(3):
+        b.count_persistent(roots, stream=stream)
+        persist_ms.append(b.stats()["ms_total"])
+    persist_ms = statistics.median(persist_ms)
     # one tc_count per graph, same GPU, same graphs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -799,8 +812,13 @@ def measure_batched(args, world, rank, local) -> dict:
         "gpu_launches": st["launches"] * args.steps,
         "launches_per_batch": st["launches"],
         "small_batch": {"graphs": len(small_ix), "edges": small_edges, "ms_per_batch": small_ms,
-                        "launches": small_launches,
-                        "what": "the 64 smallest graphs as one batch: the fixed cost of a batch"},
+                        "launches": small_launches, "persistent_ms_per_batch": small_persist_ms,
+                        "what": "the 64 smallest graphs as one batch: the fixed cost of a batch; "
+                                "persistent = tc_batch_count_persistent (one launch)"},
+        "persistent": {"ms_per_batch": persist_ms, "graphs_per_s": len(gs) / (persist_ms / 1e3),
+                       "launches": 1,
+                       "what": "tc_batch_count_persistent: the whole batch in one launch, one "
+                               "graph per block (the same counts)"},
         "clocks": clk,
     }
 

@@ -300,6 +300,20 @@ tc_status tc_batch_create_from_edges(const uint32_t* src, const uint32_t* dst,
 tc_status tc_batch_max_degree_vertices(tc_batch* b, void* stream, uint32_t* host_roots);
 /* roots[i] < n_i of graph i (ignored for empty graphs); counts: host, k entries. */
 tc_status tc_batch_count(tc_batch* b, const uint32_t* roots, void* stream, uint64_t* counts);
+/*
+ * The same counts (and levels, for tc_batch_get_levels) from ONE persistent
+ * launch: each block takes whole graphs from a device work queue, largest
+ * first, and runs the path for a graph inside the block -- BFS from its root
+ * and the restart rule of Algorithm CETC-Seq, the cover edges (Theorem
+ * "Cover-Edge Set Generation") and their intersections under the counting
+ * rule of Algorithm CETC-Seq.  Meant for batches of many small graphs (a few
+ * million edges each at most: a graph is one block's work).  The first call on
+ * a batch also sorts its graphs by size (one extra launch and synchronisation).
+ * Statistics: ms_total, the batch's triangles, c1, c2 and cover edges.
+ * Errors as tc_batch_count.
+ */
+tc_status tc_batch_count_persistent(tc_batch* b, const uint32_t* roots, void* stream,
+                                    uint64_t* counts);
 tc_status tc_batch_set_params(tc_batch* b, const tc_params* p);
 /* Statistics of the last tc_batch_count, summed over the batch. */
 tc_status tc_batch_get_stats(const tc_batch* b, tc_stats* out);

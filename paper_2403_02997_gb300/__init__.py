@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "tc_bfs_levels_noalloc": ([vp, vp, u32, u32, vp, vp], ctypes.c_int),
         "tc_batch_create": ([P(vp), ctypes.c_size_t, vp, P(vp)], ctypes.c_int),
         "tc_batch_count": ([vp, P(u32), vp, P(u64)], ctypes.c_int),
+        "tc_batch_count_persistent": ([vp, P(u32), vp, P(u64)], ctypes.c_int),
         "tc_batch_set_params": ([vp, P(tc_params)], ctypes.c_int),
         "tc_batch_get_stats": ([vp, P(tc_stats)], ctypes.c_int),
         "tc_batch_get_levels": ([vp, ctypes.c_size_t, vp], ctypes.c_int),
@@ -467,6 +468,14 @@ class Batch:
         out = (ctypes.c_uint64 * self.k)()
         _check(load_library().tc_batch_count(self.handle, rs, _stream_handle(stream), out),
                "tc_batch_count")
+        return [int(x) for x in out]
+
+    def count_persistent(self, roots: Sequence[int], stream=None) -> list:
+        """The same counts from one persistent launch, one graph per block (small graphs)."""
+        rs = (ctypes.c_uint32 * self.k)(*roots)
+        out = (ctypes.c_uint64 * self.k)()
+        _check(load_library().tc_batch_count_persistent(self.handle, rs, _stream_handle(stream),
+                                                        out), "tc_batch_count_persistent")
         return [int(x) for x in out]
 
     def set_params(self, **kw) -> None:

@@ -27,6 +27,8 @@ struct tc_batch {
   unsigned long long* eoff = nullptr;
   unsigned long long* gcount = nullptr;
   uint32_t* roots = nullptr;               // device, k
+  uint32_t* order = nullptr;               // device, k: graphs largest first (persistent count)
+  std::vector<uint32_t> order_h;           // host copy, made on the first persistent count
 };
 
 namespace tc {
@@ -110,6 +112,14 @@ __global__ void __launch_bounds__(kGatherBlock) k_batch_maxdeg(
   }
 }
 
+// Entry offsets of the graphs: out[g] = row_ptr[voff[g]], g = 0..k.
+__global__ void k_graph_entries(const unsigned long long* __restrict__ row_ptr,
+                                const unsigned long long* __restrict__ voff, uint32_t k,
+                                unsigned long long* __restrict__ out) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= k; g += gridDim.x * blockDim.x)
+    out[g] = row_ptr[voff[g]];
+}
+
 // Counters, host mirror and events of a union handle (a pooled handle's
 // mirror is pageable: freeing pinned memory would synchronise the device).
 tc_status init_union(tc_graph* u, cudaStream_t st) {
@@ -144,6 +154,7 @@ void free_batch(tc_batch* b) {
   dev_free(u, b->eoff, fs);
   dev_free(u, b->gcount, fs);
   dev_free(u, b->roots, fs);
+  dev_free(u, b->order, fs);
   if (u) {
     u->voff = nullptr;
     u->gcount = nullptr;
@@ -414,6 +425,69 @@ tc_status tc_batch_count(tc_batch* b, const uint32_t* roots, void* stream, uint6
   u->stats.launches = g_launches - launches0;
   u->stats.hash_items = c.items;
   u->stats.hash_edges = c.num_large;
+  u->counted = true;
+  return TC_OK;
+}
+
+tc_status tc_batch_count_persistent(tc_batch* b, const uint32_t* roots, void* stream,
+                                    uint64_t* counts) {
+  if (!b || !roots || !counts) return TC_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tc_graph* u = b->u;
+  const uint32_t k = b->k;
+  std::vector<uint32_t> gr(k, 0);
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t n = b->part_n[i];
+    if (n == 0) continue;
+    if (roots[i] >= n) return TC_ERR_INVALID_ARG;
+    gr[i] = (uint32_t)(b->voff_h[i] + roots[i]);
+  }
+  std::memset(&u->stats, 0, sizeof(u->stats));
+  u->stats.m = u->m;
+  u->counted = false;
+  const uint32_t launches0 = g_launches;
+  if (!b->order) {  // once per batch: the graphs by entries, largest first
+    unsigned long long* ent = nullptr;
+    TC_CUDA_TRY(dev_alloc(u, &ent, (size_t)k + 1, st));
+    k_graph_entries<<<grid_for(k + 1, 256, 64), 256, 0, st>>>(u->row_ptr, b->voff, k, ent); TC_LAUNCHED();
+    std::vector<unsigned long long> eh(k + 1);
+    cudaError_t e = cudaMemcpyAsync(eh.data(), ent, sizeof(unsigned long long) * (k + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(u, ent, st);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e);
+      return TC_ERR_CUDA;
+    }
+    b->order_h.resize(k);
+    for (uint32_t i = 0; i < k; ++i) b->order_h[i] = i;
+    std::stable_sort(b->order_h.begin(), b->order_h.end(), [&](uint32_t x, uint32_t y) {
+      return eh[x + 1] - eh[x] > eh[y + 1] - eh[y];
+    });
+    TC_CUDA_TRY(dev_alloc(u, &b->order, k, st));
+    TC_CUDA_TRY(cudaMemcpyAsync(b->order, b->order_h.data(), sizeof(uint32_t) * k,
+                                cudaMemcpyHostToDevice, st));
+  }
+  TC_CUDA_TRY(cudaEventRecord(u->ev[0], st));
+  TC_CUDA_TRY(cudaMemcpyAsync(b->roots, gr.data(), sizeof(uint32_t) * k, cudaMemcpyHostToDevice,
+                              st));
+  TC_TRY(run_batch_graphs(u, b->voff, b->roots, b->order, k, b->gcount, st));
+  TC_CUDA_TRY(cudaEventRecord(u->ev[3], st));
+  std::vector<unsigned long long> gc(k);
+  TC_CUDA_TRY(cudaMemcpyAsync(gc.data(), b->gcount, sizeof(unsigned long long) * k,
+                              cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaMemcpyAsync(u->ctr_host, u->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  TC_CUDA_TRY(cudaStreamSynchronize(st));
+  const DevCounters& c = *u->ctr_host;
+  if (c.err) return TC_ERR_CUDA;
+  for (uint32_t i = 0; i < k; ++i) counts[i] = gc[i];
+  u->stats.triangles = c.tri;
+  u->stats.c1 = c.c1;
+  u->stats.c2 = c.c2;
+  u->stats.num_cover = c.num_cover;
+  cudaEventElapsedTime(&u->stats.ms_total, u->ev[0], u->ev[3]);
+  u->stats.ms_intersect = u->stats.ms_total;
+  u->stats.launches = g_launches - launches0;
   u->counted = true;
   return TC_OK;
 }

@@ -960,6 +960,286 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
   flush_tally(tl, ctr);
 }
 
+// ---- a batch counted in one persistent launch, one graph per block ---------
+//
+// k_batch_graphs takes the graphs of a batch from a device work queue (largest
+// first) and runs the whole path for a graph inside one block of kFuseThreads
+// threads: BFS levels from its root (top-down, the frontier's edges spread
+// over the block by a scan of its degrees), the restart rule (union-find over
+// the still-unvisited vertices, each root the smallest id of its component,
+// then one multi-source BFS from those roots), the cover-edge scan, and the
+// intersections under the counting rule of Algorithm CETC-Seq.  A graph's CSR
+// (a few MB at most in the batches it serves) stays in L2 while its block
+// works on it.  Everything a graph needs lives in its own slices of the
+// union's arrays: level / queues / parents over its vertices, the pairs of
+// high-degree cover edges over its half of the entries.
+//  - both degrees <= small_max: the cover edge is queued per warp and merged
+//    by one lane (block_merge);
+//  - otherwise: a warp takes the pair and each lane binary-searches every
+//    32nd id of the shorter row in the longer one.
+constexpr int kFuseThreads = 1024;
+constexpr int kFuseWarps = kFuseThreads / kWarp;
+
+// Block-level BFS: levels lvl0 + 1, ... from the qlen vertices in q (all at
+// level lvl0), queues q / nq ping-ponging; all threads call it.  Each level
+// takes the frontier in tiles of kFuseThreads vertices; a block scan of their
+// degrees hands every thread whole edges, so a hub's row is spread over the
+// block.  A vertex is claimed with atomicCAS(level, -1, l + 1).
+__device__ void block_bfs(const unsigned long long* __restrict__ row_ptr,
+                          const uint32_t* __restrict__ col, int32_t* level, uint32_t* q,
+                          uint32_t* nq, uint32_t qlen, int32_t lvl0, uint32_t* s_v,
+                          unsigned long long* s_b, unsigned long long* s_off,
+                          unsigned long long* s_tmp, uint32_t* s_len) {
+  const unsigned lane = lane_id();
+  int32_t lvl = lvl0;
+  while (qlen > 0) {
+    if (threadIdx.x == 0) *s_len = 0;
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < qlen; t0 += kFuseThreads) {
+      const uint32_t i = t0 + threadIdx.x;
+      const uint32_t u = i < qlen ? __ldcg(q + i) : kNoLevel;
+      unsigned long long b = 0, d = 0;
+      if (u != kNoLevel) {
+        b = row_ptr[u];
+        d = row_ptr[u + 1] - b;
+      }
+      unsigned long long total;
+      const unsigned long long off = block_exclusive_scan(d, s_tmp, &total);
+      s_v[threadIdx.x] = u;
+      s_b[threadIdx.x] = b;
+      s_off[threadIdx.x] = off;
+      __syncthreads();
+      const uint32_t tv = min((uint32_t)kFuseThreads, qlen - t0);
+      for (unsigned long long j0 = 0; j0 < total; j0 += kFuseThreads) {
+        const unsigned long long j = j0 + threadIdx.x;
+        bool take = false;
+        uint32_t w = 0;
+        if (j < total) {
+          uint32_t lo = 0, hi = tv - 1;  // last vertex of the tile whose edges start at or before j
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+          }
+          w = col[s_b[lo] + (j - s_off[lo])];
+          take = atomicCAS(&level[w], -1, lvl + 1) == -1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (m) {
+          const unsigned leader = __ffs(m) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(s_len, (uint32_t)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (take) nq[base + __popc(m & ((1u << lane) - 1u))] = w;
+        }
+      }
+      __syncthreads();  // s_v / s_b / s_off are rewritten by the next tile
+    }
+    qlen = *s_len;
+    uint32_t* t = q;
+    q = nq;
+    nq = t;
+    ++lvl;
+    __syncthreads();  // every thread has read *s_len before it is reset
+  }
+}
+
+// Union-find over the graph's unvisited vertices: the larger root is hooked
+// under the smaller with a CAS, so a root is always the smallest id of its
+// tree (find with path halving; any ancestor is a valid parent).
+__device__ __forceinline__ uint32_t fuse_find(uint32_t* parent, uint32_t x) {
+  uint32_t p = parent[x];
+  while (p != x) {
+    const uint32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;
+    x = p;
+    p = gp;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(kFuseThreads, 1) k_batch_graphs(
+    const unsigned long long* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+    const uint32_t* __restrict__ erow, int32_t* level, uint32_t* qa, uint32_t* qb,
+    uint32_t* parent, uint2* pairs, const unsigned long long* __restrict__ voff,
+    const uint32_t* __restrict__ roots, const uint32_t* __restrict__ order, uint32_t k,
+    uint32_t small_max, unsigned long long* __restrict__ gcount, DevCounters* ctr) {
+  __shared__ uint32_t s_v[kFuseThreads];
+  __shared__ unsigned long long s_b[kFuseThreads], s_off[kFuseThreads];
+  __shared__ unsigned long long s_tmp[kFuseWarps + 1];
+  __shared__ uint2 s_q[kFuseWarps][kSmallQueue];
+  __shared__ uint32_t s_g, s_len, s_npairs;
+  const unsigned lane = lane_id(), warp = threadIdx.x / kWarp;
+  uint2* const q = s_q[warp];
+  Tally tl;
+  for (;;) {
+    if (threadIdx.x == 0) s_g = (uint32_t)atomicAdd(&ctr->item_cursor, 1ull);
+    __syncthreads();
+    if (s_g >= k) break;
+    const uint32_t g = order[s_g];
+    const unsigned long long v0 = voff[g], v1 = voff[g + 1];
+    const unsigned long long E0 = row_ptr[v0], E1 = row_ptr[v1];
+    unsigned long long hits = 0, covers = 0;  // this thread's, in graph g
+    if (v1 > v0) {
+      // ---- levels: BFS from the root, then the restart rule
+      for (unsigned long long v = v0 + threadIdx.x; v < v1; v += kFuseThreads) level[v] = -1;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const uint32_t r = roots[g];
+        level[r] = 0;
+        qa[v0] = r;
+      }
+      __syncthreads();
+      block_bfs(row_ptr, col, level, qa + v0, qb + v0, 1, 0, s_v, s_b, s_off, s_tmp, &s_len);
+      unsigned long long left = 0;
+      for (unsigned long long v = v0 + threadIdx.x; v < v1; v += kFuseThreads) {
+        const bool un = level[v] == -1;
+        left += un;
+        if (un) parent[v] = (uint32_t)v;
+      }
+      left = block_sum(left, s_tmp);
+      if (left) {
+        // union-find over the unvisited vertices (every edge of one joins two)
+        for (unsigned long long j = E0 + threadIdx.x; j < E1; j += kFuseThreads) {
+          const uint32_t u = erow[j], w = col[j];
+          if (w >= u || level[u] != -1) continue;
+          uint32_t a = u, c = w;
+          for (;;) {
+            a = fuse_find(parent, a);
+            c = fuse_find(parent, c);
+            if (a == c) break;
+            const uint32_t hi = a > c ? a : c, lo = a > c ? c : a;
+            if (atomicCAS(&parent[hi], hi, lo) == hi) break;
+          }
+        }
+        if (threadIdx.x == 0) s_len = 0;
+        __syncthreads();
+        // the roots (each its component's smallest id) seed one multi-source BFS
+        for (unsigned long long v0b = v0; v0b < v1; v0b += kFuseThreads) {
+          const unsigned long long v = v0b + threadIdx.x;
+          const bool seed = v < v1 && level[v] == -1 && parent[v] == (uint32_t)v;
+          if (seed) level[v] = 0;
+          const unsigned m = __ballot_sync(0xffffffffu, seed);
+          if (m) {
+            const unsigned leader = __ffs(m) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&s_len, (uint32_t)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (seed) qa[v0 + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)v;
+          }
+        }
+        __syncthreads();
+        const uint32_t seeds = s_len;
+        __syncthreads();
+        block_bfs(row_ptr, col, level, qa + v0, qb + v0, seeds, 0, s_v, s_b, s_off, s_tmp,
+                  &s_len);
+      }
+      // ---- cover edges: small pairs merged by a lane, the others listed
+      if (threadIdx.x == 0) s_npairs = 0;
+      __syncthreads();
+      uint2* gp = pairs + E0 / 2;  // the graph's half of the entries: room for all its edges
+      uint32_t qn = 0;
+      for (unsigned long long j0 = E0; j0 < E1; j0 += kFuseThreads) {
+        const unsigned long long j = j0 + threadIdx.x;
+        bool is_cover = false;
+        uint2 ce = make_uint2(0, 0);
+        if (j < E1) {
+          const uint32_t u = erow[j], v = col[j];
+          if (v > u && level[v] == level[u]) {
+            is_cover = true;
+            ce = make_uint2(u, v);
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, is_cover);
+        if (is_cover) q[qn + __popc(m & ((1u << lane) - 1u))] = ce;
+        qn += __popc(m);
+        const bool last = j0 + kFuseThreads >= E1;
+        while (qn >= kWarp || (last && qn)) {
+          // every lane bins one queued cover edge (the last step drains the rest)
+          __syncwarp();
+          const uint32_t take = min(qn, (uint32_t)kWarp);
+          bool big = false;
+          uint2 e = make_uint2(0, 0);
+          if (lane < take) {
+            e = q[lane];
+            ++covers;
+            const unsigned long long bu = row_ptr[e.x], eu = row_ptr[e.x + 1];
+            const unsigned long long bv = row_ptr[e.y], ev = row_ptr[e.y + 1];
+            if (eu - bu <= small_max && ev - bv <= small_max) {
+              const int32_t lu = level[e.x];
+              const uint32_t vv = e.y;
+              block_merge(col, bu, eu, bv, ev, [&](uint32_t w) {
+                if (level[w] != lu) {
+                  ++tl.c1;
+                  ++hits;
+                } else if (vv < w) {
+                  ++tl.c2c;
+                  ++hits;
+                }
+              });
+            } else {
+              big = true;
+            }
+          }
+          const unsigned mb = __ballot_sync(0xffffffffu, big);
+          if (mb) {
+            const unsigned leader = __ffs(mb) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&s_npairs, (uint32_t)__popc(mb));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (big) gp[base + __popc(mb & ((1u << lane) - 1u))] = e;
+          }
+          __syncwarp();
+          if (lane + take < qn) q[lane] = q[take + lane];
+          qn -= take;
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // ---- pairs with a high-degree endpoint: a warp per pair, each lane
+      // binary-searching every 32nd id of the shorter row in the longer one
+      const uint32_t np = s_npairs;
+      for (uint32_t p = warp; p < np; p += kFuseWarps) {
+        const uint2 e = gp[p];
+        const uint32_t u = e.x, v = e.y;
+        const int32_t lu = level[u];
+        const unsigned long long bu = row_ptr[u], eu = row_ptr[u + 1];
+        const unsigned long long bv = row_ptr[v], ev = row_ptr[v + 1];
+        const bool u_short = eu - bu <= ev - bv;
+        const unsigned long long sb = u_short ? bu : bv, se = u_short ? eu : ev;
+        const unsigned long long lb = u_short ? bv : bu, le = u_short ? ev : eu;
+        unsigned long long lo = lb;
+        for (unsigned long long t = sb + lane; t < se; t += kWarp) {
+          const uint32_t w = col[t];
+          unsigned long long a = lo, b = le;
+          while (a < b) {
+            const unsigned long long mid = a + (b - a) / 2;
+            if (col[mid] < w) a = mid + 1; else b = mid;
+          }
+          lo = a;
+          if (a < le && col[a] == w) {
+            if (level[w] != lu) {
+              ++tl.c1;
+              ++hits;
+            } else if (v < w) {
+              ++tl.c2c;
+              ++hits;
+            }
+          }
+        }
+      }
+    }
+    // ---- the graph's count
+    hits = block_sum(hits, s_tmp);
+    covers = block_sum(covers, s_tmp);
+    if (threadIdx.x == 0) {
+      gcount[g] = hits;
+      if (covers) atomicAdd(&ctr->num_cover, covers);
+    }
+    __syncthreads();
+  }
+  flush_tally(tl, ctr);
+}
+
 }  // namespace
 
 namespace {
@@ -1261,6 +1541,20 @@ tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
   TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t need = owner_hash_smem(chunk) + fa.sharedSizeBytes;
   return need <= (size_t)optin ? TC_OK : TC_ERR_INVALID_ARG;
+}
+
+tc_status run_batch_graphs(tc_graph* u, const unsigned long long* voff, const uint32_t* roots,
+                           const uint32_t* order, uint32_t k, unsigned long long* gcount,
+                           cudaStream_t st) {
+  TC_CUDA_TRY(cudaMemsetAsync(u->ctr, 0, sizeof(DevCounters), st));
+  TC_CUDA_TRY(cudaEventRecord(u->ev[4], st));
+  if (k == 0) return TC_OK;
+  const uint32_t small_max = u->params.small_max_degree;
+  k_batch_graphs<<<num_sms(), kFuseThreads, 0, st>>>(
+      u->row_ptr, u->col, u->erow, u->level, u->queue_a, u->queue_b, u->parent, u->large, voff,
+      roots, order, k, small_max, gcount, u->ctr); TC_LAUNCHED();
+  TC_CUDA_TRY(cudaGetLastError());
+  return TC_OK;
 }
 
 tc_status fill_entry_rows(tc_graph* g, cudaStream_t st) {

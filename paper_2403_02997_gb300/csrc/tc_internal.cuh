@@ -214,6 +214,12 @@ __device__ __forceinline__ uint32_t batch_graph_of(const unsigned long long* off
   return lo;
 }
 tc_status run_cover_and_count(tc_graph* g, cudaStream_t st);
+// A batch union's graphs counted in one persistent launch, one graph per block
+// (k_batch_graphs): roots[g] is graph g's root as a union id, order[] the
+// graphs in the order blocks take them; counts to gcount[g], totals to u->ctr.
+tc_status run_batch_graphs(tc_graph* u, const unsigned long long* voff, const uint32_t* roots,
+                           const uint32_t* order, uint32_t k, unsigned long long* gcount,
+                           cudaStream_t st);
 // g->erow[j] = the row of adjacency entry j (after the CSR is built; once per
 // graph: the per-count entry loops read it instead of searching row_ptr).
 tc_status fill_entry_rows(tc_graph* g, cudaStream_t st);

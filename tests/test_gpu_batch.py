@@ -134,3 +134,43 @@ def test_batch_from_edge_lists():
         tc.Batch.from_edges([(s1, d1, 5), (np.array([0, 7], np.uint32),
                                              np.array([1, 2], np.uint32), 6)])
     assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("params", [{}, dict(small_max_degree=0), dict(small_max_degree=1 << 30),
+                                    dict(small_max_degree=8)])
+def test_persistent_batch_counts_and_levels(params):
+    """One persistent launch, one graph per block: every graph's count and levels equal the
+    oracle's, with every cover edge merged by a lane (small_max_degree huge), searched by a warp
+    (0), or split between the two; a second call (graph order cached) and the union path agree."""
+    items = mixed_graphs()
+    s, d = gen.rmat_edges(14, 16, 3)          # frontiers of thousands of vertices, hub pairs
+    items.append((1 << 14, s, d, "maxdeg"))
+    want, roots, levels = oracle_truth(items)
+    gs = [tc.Graph(s_, d_, n) for n, s_, d_, _ in items]
+    try:
+        b = tc.Batch(gs)
+        if params:
+            b.set_params(**params)
+        assert b.count_persistent(roots) == want
+        for i, lv in enumerate(levels):
+            assert np.array_equal(b.levels(i), lv), i
+        st = b.stats()
+        assert st["triangles"] == sum(want) and st["c2"] % 3 == 0
+        assert b.count(roots) == want
+        assert b.count_persistent(roots) == want
+        b.close()
+    finally:
+        for g in gs:
+            g.close()
+
+
+def test_persistent_batch_from_edge_lists():
+    items = mixed_graphs()
+    want, roots, levels = oracle_truth(items)
+    b = tc.Batch.from_edges([(s, d, n) for n, s, d, _ in items])
+    try:
+        assert b.count_persistent(roots) == want
+        for i, lv in enumerate(levels):
+            assert np.array_equal(b.levels(i), lv), i
+    finally:
+        b.close()
