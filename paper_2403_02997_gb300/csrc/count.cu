@@ -873,12 +873,24 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
                        s_be[i] > nnz_cap, ctr))
         s_a[i] = s_ae[i] = s_b[i] = s_be[i] = 0;
     }
-    for (uint32_t c = 0; c < chunks; ++c) {
-      const unsigned long long cb = hb + (unsigned long long)c * chunk;
-      const unsigned long long ce = min(he, cb + chunk);
+    // An owner whose row spans several chunks is taken in its two level parts
+    // (the other-level and the same-level neighbours of the level-split row,
+    // each sorted): a streamer's other-level ids can only meet the owner's
+    // other-level neighbours, and its same-level ids above v only the owner's
+    // same-level ones, so each segment passes over its own part's chunks only.
+    // A single-chunk owner keeps one table of its whole row.
+    const bool split = !kPlain && chunks > 1;
+    const unsigned long long hs = split ? rows.se[h] : he;  // start of the same-level part
+    const uint32_t* __restrict__ tsrc = split ? lcol : col;
+    for (uint32_t part = 0; part < (split ? 2u : 1u); ++part) {
+      const unsigned long long pb = part ? hs : hb, pe = split && !part ? hs : he;
+      const uint32_t pchunks = (uint32_t)((pe - pb + chunk - 1) / chunk);
+    for (uint32_t c = 0; c < pchunks; ++c) {
+      const unsigned long long cb = pb + (unsigned long long)c * chunk;
+      const unsigned long long ce = min(pe, cb + chunk);
       const uint32_t entries = (uint32_t)(ce - cb);
-      const bool bounded = c + 1 < chunks;
-      const uint32_t hi_id = bounded ? col[ce - 1] : kEmpty;
+      const bool bounded = c + 1 < pchunks;
+      const uint32_t hi_id = bounded ? tsrc[ce - 1] : kEmpty;
       // two tables of >= 5/4 x entries slots each (load <= 0.4)
       const uint32_t size = entries + entries / 4 + 1;
       const Cuckoo ck{size};
@@ -893,8 +905,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         // dependent load latency per entry
         unsigned long long j = cb + threadIdx.x;
         for (; j + 3 * blockDim.x < ce; j += 4 * blockDim.x) {
-          const uint32_t w0 = col[j], w1 = col[j + blockDim.x], w2 = col[j + 2 * blockDim.x],
-                         w3 = col[j + 3 * blockDim.x];
+          const uint32_t w0 = tsrc[j], w1 = tsrc[j + blockDim.x], w2 = tsrc[j + 2 * blockDim.x],
+                         w3 = tsrc[j + 3 * blockDim.x];
           bool ok = ck.insert(w0);
           ok = ck.insert(w1) && ok;
           ok = ck.insert(w2) && ok;
@@ -902,12 +914,12 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
           if (!ok) s_fail = 1;
         }
         for (; j < ce; j += blockDim.x)
-          if (!ck.insert(col[j])) s_fail = 1;
+          if (!ck.insert(tsrc[j])) s_fail = 1;
       }
       __syncthreads();
       const bool sorted = s_fail != 0;
       if (sorted) {  // rare: keep the chunk as a sorted array instead
-        for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_table[i] = col[cb + i];
+        for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_table[i] = tsrc[cb + i];
         __syncthreads();
       }
       for (;;) {
@@ -915,8 +927,11 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         if (lane == 0) i = atomicAdd(&s_next, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= ne) break;
-        const unsigned long long a = s_a[i], b = s_b[i];
+        // with the row split, part 0 streams only the other-level segment and
+        // part 1 only the same-level one (the other passed in empty)
         const unsigned long long ae = s_ae[i], be = s_be[i];
+        const unsigned long long a = split && part ? ae : s_a[i];
+        const unsigned long long b = split && !part ? be : s_b[i];
         Emit ed = em;
         if (kEmit) {
           const uint32_t x = s_x[i];
@@ -938,8 +953,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
           }
         }
         if (lane == 0) {
-          s_a[i] = r.a;
-          s_b[i] = r.b;
+          if (!(split && part)) s_a[i] = r.a;
+          if (!(split && !part)) s_b[i] = r.b;
         }
         const uint32_t c1 = r.c1, c2c = r.c2c;
         if (kPlain && plain_as_c2) {
@@ -951,6 +966,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         item_hits += c1 + c2c;
       }
       __syncthreads();
+    }
     }
     if (nb) {  // one atomic per warp per item into the owner's graph
       item_hits = warp_sum(item_hits);
