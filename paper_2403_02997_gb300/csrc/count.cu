@@ -17,11 +17,13 @@
 //                list.  If both degrees are <= small_max_degree the thread merges
 //                the two rows itself (two pointers, Algorithm EMP); otherwise the
 //                edge goes to its endpoint of larger degree, the "owner".
-// k_level_split  per row x: a copy of N(x) reordered as [neighbours on another
-//                level | neighbours on L(x)], each part ascending (a stable
+// k_level_split  per row x: a copy of N(x) reordered as [neighbours on L(x) |
+//                neighbours on another level], each part ascending (a stable
 //                partition; rows up to kSplitMax by one warp, longer rows in
 //                tiles of kSplitTile by k_split_tile_*).  A streamer then skips
-//                its same-level neighbours w <= v, which can never count.
+//                its same-level neighbours w <= v, which can never count, and
+//                what it streams -- its same-level neighbours above v, then
+//                all its other-level ones -- is one contiguous range.
 // k_bucket       groups the owner-path edges by owner (counting sort).
 // k_owner_hash   one CTA per work item (owner h, slice of h's cover edges):
 //                N(h) is taken in chunks; each chunk goes into a shared-memory
@@ -452,7 +454,8 @@ __global__ void __launch_bounds__(kWarpMergeBlock) k_warp_merge(
 
 // One warp per row of degree <= kSplitMax (grid-stride).  Pass 1 counts the
 // neighbours on another level; pass 2 writes both parts in order with ballot
-// ranks.  Longer rows are left to the tile kernels below.
+// ranks, the same-level part first.  lsplit[x] is where the other-level part
+// starts.  Longer rows are left to the tile kernels below.
 __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
                               const uint32_t* __restrict__ col, const int32_t* __restrict__ level,
                               uint32_t n, uint32_t* __restrict__ lcol,
@@ -474,7 +477,7 @@ __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
       const bool o = j < e && level[col[j]] != lx;
       other += __popc(__ballot_sync(0xffffffffu, o));
     }
-    unsigned long long po = b, ps = b + other;
+    unsigned long long ps = b, po = e - other;
     for (unsigned long long j0 = b; j0 < e; j0 += 32) {
       const unsigned long long j = j0 + lane;
       uint32_t w = 0;
@@ -493,7 +496,7 @@ __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
       po += __popc(mo);
       ps += __popc(ms);
     }
-    if (lane == 0) lsplit[x] = b + other;
+    if (lane == 0) lsplit[x] = e - other;
   }
 }
 
@@ -575,15 +578,15 @@ __global__ void __launch_bounds__(kTileBlock) k_split_tile_write(
   unsigned long long tot;
   unsigned long long po = block_exclusive_scan((unsigned long long)mine, tmp, &tot);
   unsigned long long ps = block_exclusive_scan((unsigned long long)(__popc(valid) - mine), tmp, &tot);
-  po += b + before;
-  ps += b + all + (k * kSplitTile - before);
+  po += e - all + before;
+  ps += b + (k * kSplitTile - before);
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     if (!(valid & (1u << i))) continue;
     if (flags & (1u << i)) lcol[po++] = w[i];
     else lcol[ps++] = w[i];
   }
-  if (k == 0 && threadIdx.x == 0) lsplit[x] = b + all;
+  if (k == 0 && threadIdx.x == 0) lsplit[x] = e - all;
 }
 
 __global__ void k_bucket(const uint2* __restrict__ large, unsigned long long count,
@@ -774,6 +777,74 @@ __device__ __forceinline__ EdgePass stream_edge(const uint32_t* __restrict__ lco
   return r;
 }
 
+// Lookups of one 128-id step (lane l holds ids l, l + 32, l + 64, l + 96),
+// tallied as c2' for the ids of position < q2 in the step and as c1 from q2
+// on; kMasked: only the step's first rem ids (rem <= 128; len = rem - lane)
+// count, and rows of 32 past them are skipped.
+template <bool kMasked, bool kEmit>
+__device__ __forceinline__ void fused_step(const uint32_t (&w)[4], int len, int rem, int q2,
+                                           const Cuckoo ck, const Emit& em, uint32_t& c1,
+                                           uint32_t& c2c) {
+  const int lane = (int)lane_id();
+  if (kMasked || (q2 > 0 && q2 < 128)) {  // per id (the last step, or the boundary's)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (kMasked && 32 * t >= rem) break;  // warp-uniform
+      uint32_t hit = ck.contains(w[t]);
+      if (kMasked) hit &= (uint32_t)(len > 32 * t);
+      if (32 * t + lane < q2) c2c += hit; else c1 += hit;
+      if (kEmit) em.put(hit, w[t]);
+    }
+  } else {  // the whole step on one side of the boundary
+    uint32_t h = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t hit = ck.contains(w[t]);
+      h += hit;
+      if (kEmit) em.put(hit, w[t]);
+    }
+    if (q2 > 0) c2c += h; else c1 += h;
+  }
+}
+
+// Against an owner of one chunk (unbounded), the two segments of a cover edge
+// as one range arr[cur, end): its same-level ids above v, [cur, bnd), tallied
+// as c2', then its other-level ids, [bnd, end), tallied as c1 -- one pass, and
+// the same-level part fills the first step of the other-level part instead of
+// taking a partial step of its own.  Same step structure as stream_segment.
+// A row holds fewer than n < 2^31 ids.
+template <bool kEmit>
+__device__ __forceinline__ void stream_fused(const uint32_t* __restrict__ arr,
+                                             unsigned long long cur, unsigned long long bnd,
+                                             unsigned long long end, const Cuckoo ck,
+                                             const Emit& em, uint32_t& c1, uint32_t& c2c) {
+  if (cur >= end) return;
+  const uint32_t lane = lane_id();
+  const uint32_t* p = arr + cur + lane;
+  uint32_t len = (uint32_t)(end - cur) - lane;  // ids from p to end (as int: may be <= 0)
+  const int rb = (int)(end - bnd);              // ids of the other-level part
+  uint32_t w[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) w[t] = (int)len > 32 * t ? __ldg(p + 32 * t) : kEmpty;
+  for (;;) {
+    const int rem = (int)(len + lane);  // ids from the step's first to end
+    const int q2 = rem - rb;            // same-level ids from the step's first on
+    if (rem > 128) {
+      uint32_t wn[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) wn[t] = (int)len > 128 + 32 * t ? __ldg(p + 128 + 32 * t) : kEmpty;
+      fused_step<false, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
+      p += 128;
+      len -= 128;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) w[t] = wn[t];
+    } else {
+      fused_step<true, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
+      return;
+    }
+  }
+}
+
 // The rare path (a chunk kept as a sorted array), out of line so it does not
 // weigh on the registers of the hot loop.  Arguments and result go by value:
 // nothing of the caller's has its address taken (which would put it in local
@@ -811,12 +882,13 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // The rows are given as HashRows.  Cover edges of Algorithm CETC-Seq
 // (kPlain = false): the owner's table is its whole row, col[tb[h], te[h]) with
 // tb = row_ptr, te = row_ptr + 1, and the streamer x streams two segments of
-// its level-split row scol = lcol: [sb[x], se[x]) (sb = row_ptr, se = lsplit:
-// the other-level part, tallied as c1) and its same-level part above v,
-// [first id > v in [se[x], te[x]), te[x]) (tallied as c2').  Plain pairs
-// (kPlain = true): the table is tcol[tb[h], te[h]) and the streamer streams the
-// one segment scol[sb[x], se[x]); hits are tallied as c1, or as c2' when
-// plain_as_c2 is set.
+// its level-split row scol = lcol = [same-level | other-level]: its other-level
+// part [sb[x], se[x]) (sb = lsplit, se = row_ptr + 1; tallied as c1) and its
+// same-level part above v, [first id > v in [tb[x], sb[x]), sb[x]) (tallied as
+// c2').  The two are adjacent: against an owner of one chunk they go as one
+// range (stream_fused).  Plain pairs (kPlain = true): the table is
+// tcol[tb[h], te[h]) and the streamer streams the one segment scol[sb[x],
+// se[x]); hits are tallied as c1, or as c2' when plain_as_c2 is set.
 template <int kThreads, bool kPlain, bool kEmit>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const HashRows rows, const unsigned long long* __restrict__ ooff,
@@ -858,16 +930,15 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         s_a[i] = s_ae[i] = s_b[i] = s_be[i] = 0;
         continue;
       }
-      const unsigned long long sp = rows.se[x];
-      s_a[i] = rows.sb[x];
-      s_ae[i] = sp;
+      const unsigned long long os = rows.sb[x];  // the other-level part: [os, se[x])
+      s_a[i] = os;
+      s_ae[i] = rows.se[x];
       if (kPlain) {
         s_b[i] = s_be[i] = 0;
-      } else {
+      } else {  // the same-level part [tb[x], os): its ids above v
         const uint32_t v = x > h ? x : h;
-        const unsigned long long xe = te[x];
-        s_b[i] = lower_bound_u32(lcol, sp, xe, v + 1);
-        s_be[i] = xe;
+        s_b[i] = lower_bound_u32(lcol, tb[x], os, v + 1);
+        s_be[i] = os;
       }
       if (check_failed(s_a[i] > s_ae[i] || s_ae[i] > nnz_cap || s_b[i] > s_be[i] ||
                        s_be[i] > nnz_cap, ctr))
@@ -880,10 +951,12 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     // same-level ones, so each segment passes over its own part's chunks only.
     // A single-chunk owner keeps one table of its whole row.
     const bool split = !kPlain && chunks > 1;
-    const unsigned long long hs = split ? rows.se[h] : he;  // start of the same-level part
+    // start of the other-level part (end of the same-level part) of h's row
+    const unsigned long long hs = split ? rows.sb[h] : hb;
     const uint32_t* __restrict__ tsrc = split ? lcol : col;
     for (uint32_t part = 0; part < (split ? 2u : 1u); ++part) {
-      const unsigned long long pb = part ? hs : hb, pe = split && !part ? hs : he;
+      // part 0: [hs, he) (the other-level part, or the whole row); part 1: [hb, hs)
+      const unsigned long long pb = part ? hb : hs, pe = part ? hs : he;
       const uint32_t pchunks = (uint32_t)((pe - pb + chunk - 1) / chunk);
     for (uint32_t c = 0; c < pchunks; ++c) {
       const unsigned long long cb = pb + (unsigned long long)c * chunk;
@@ -940,8 +1013,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         }
         EdgePass r;
         if (!sorted) {
-          if (bounded) r = stream_edge<true, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
-          else r = stream_edge<false, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
+          if (bounded) {
+            r = stream_edge<true, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
+          } else if (kPlain || split) {
+            r = stream_edge<false, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
+          } else {  // one chunk: [b, be) and [a, ae) are adjacent (be == a)
+            r = EdgePass{ae, be, 0, 0};
+            stream_fused<kEmit>(lcol, b, be, ae, ck, ed, r.c1, r.c2c);
+          }
         } else {
           r = stream_edge_sorted<kEmit>(lcol, a, ae, b, be, bounded, hi_id, entries, ed);
         }
@@ -1364,7 +1443,7 @@ __global__ void __launch_bounds__(kCoverBlock) k_forward_pairs(
 // The cover edges of Algorithm CETC-Seq-S: one thread per adjacency entry
 // (u, v); a horizontal edge with u < v joins the cover list, and the
 // intersection of its endpoints' G1 rows (the other-level parts of the
-// level-split rows, lcol[row_ptr[x], lsplit[x])) is merged by the thread when
+// level-split rows, lcol[lsplit[x], row_ptr[x + 1])) is merged by the thread when
 // both have at most small_max ids, else sent to the owner-hash pass (owner:
 // the longer G1 row, ties larger id).  Hits are tallied as c1.
 __global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
@@ -1388,8 +1467,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_g1_pairs(
         if (v > u && level[v] == level[u]) {
           is_cover = true;
           ce = make_uint2(u, v);
-          const unsigned long long bu = row_ptr[u], eu = lsplit[u];
-          const unsigned long long bv = row_ptr[v], ev = lsplit[v];
+          const unsigned long long bu = lsplit[u], eu = row_ptr[u + 1];
+          const unsigned long long bv = lsplit[v], ev = row_ptr[v + 1];
           const unsigned long long du = eu - bu, dv = ev - bv;
           if (du > 0 && dv > 0) {
             if (du <= small_max && dv <= small_max) {
@@ -1608,7 +1687,7 @@ tc_status run_cover_and_count(tc_graph* g, cudaStream_t st) {
   }
   if (nlarge == 0) return TC_OK;
   TC_TRY(run_level_split(g, st));
-  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->row_ptr, g->lsplit, g->lcol};
+  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->lsplit, g->row_ptr + 1, g->lcol};
   return run_owner_pass<false>(g, nlarge, rows, 0, g->voff, g->batch_k, g->gcount, st);
 }
 
@@ -1693,12 +1772,12 @@ tc_status run_split_count(tc_graph* g, cudaStream_t st) {
   unsigned long long nlarge = 0;
   TC_TRY(scan_owners(g, st, &nlarge));
   if (nlarge > 0) {
-    const HashRows rows{g->row_ptr, g->lsplit, g->lcol, g->row_ptr, g->lsplit, g->lcol};
+    const HashRows rows{g->lsplit, g->row_ptr + 1, g->lcol, g->lsplit, g->row_ptr + 1, g->lcol};
     TC_TRY(run_owner_pass<true>(g, nlarge, rows, 0, nullptr, 0, nullptr, st));
   }
   // T0: Algorithm forward-hashed on G0, tallied as c2' (c2 = 3 T0)
   unsigned long long total = 0;
-  TC_TRY(orient(g, g->lsplit, g->row_ptr + 1, g->lcol, st, &total));
+  TC_TRY(orient(g, g->row_ptr, g->lsplit, g->lcol, st, &total));
   return forward_pairs(g, total, 1, st);
 }
 
@@ -1732,7 +1811,7 @@ tc_status run_cover_and_list(tc_graph* g, const EmitSink& sink, cudaStream_t st)
   TC_TRY(scan_owners(g, st, &nlarge));
   if (nlarge == 0) return TC_OK;
   TC_TRY(run_level_split(g, st));
-  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->row_ptr, g->lsplit, g->lcol};
+  const HashRows rows{g->row_ptr, g->row_ptr + 1, g->col, g->lsplit, g->row_ptr + 1, g->lcol};
   return run_owner_pass<false, true>(g, nlarge, rows, 0, nullptr, 0, nullptr, st, em);
 }
 

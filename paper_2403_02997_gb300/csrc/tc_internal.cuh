@@ -90,8 +90,8 @@ struct tc_graph {
   uint2* large = nullptr;        // [m]  (owner, streamer) of owner-hash cover edges
   uint2* medium = nullptr;       // [m]  (u, v) cover edges of the warp-merge bin
   uint32_t* ostream = nullptr;   // [m]  streamers bucketed by owner
-  uint32_t* lcol = nullptr;      // [nnz] rows reordered [other-level | same-level] per count
-  unsigned long long* lsplit = nullptr;  // [n] start of the same-level part of each row
+  uint32_t* lcol = nullptr;      // [nnz] rows reordered [same-level | other-level] per count
+  unsigned long long* lsplit = nullptr;  // [n] start of the other-level part of each row
   unsigned long long* obeg = nullptr;  // [n+1] oriented adjacency A+() (forward counts), on first use
   uint32_t* ocol = nullptr;            // [m]
   uint32_t* tile_row = nullptr;  // [tile_cap] row of each tile of a long row (level split)
