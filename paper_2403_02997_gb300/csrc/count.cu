@@ -697,6 +697,64 @@ __device__ __forceinline__ uint32_t chunk_hit(const Cuckoo ck, uint32_t sorted_l
 // past its part (read again by the next chunk).  In the last step, whole rows
 // of 32 ids past end or above hi are skipped and the rest is masked per id.  A
 // segment is one row's part: shorter than n < 2^31.
+// One step's ids at p (lane l: p[0], p[32], p[64], p[96], p = the step's
+// start + l), kEmpty from len on (len = ids from p to the end, as int); a
+// step wholly before the end (full, warp-uniform) loads without per-id tests.
+__device__ __forceinline__ void load_step(const uint32_t* p, uint32_t len, bool full,
+                                          uint32_t (&w)[4]) {
+  if (full) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) w[t] = __ldg(p + 32 * t);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) w[t] = (int)len > 32 * t ? __ldg(p + 32 * t) : kEmpty;
+  }
+}
+
+// One step of stream_segment on the ids in w, the next step's loaded into wn
+// first (p, len: this step's; advanced to the next).  Returns true after the
+// last step, with the new cursor in out.
+template <bool kBounded, bool kSorted, bool kEmit>
+__device__ __forceinline__ bool segment_step(const uint32_t* __restrict__ arr, const uint32_t*& p,
+                                             uint32_t& len, const uint32_t (&w)[4],
+                                             uint32_t (&wn)[4], const uint32_t hi,
+                                             const Cuckoo ck, const uint32_t sorted_len,
+                                             const Emit& em, uint32_t& hits,
+                                             unsigned long long& out) {
+  const uint32_t lane = lane_id();
+  const int rem = (int)(len + lane);  // ids from the step's first to the end
+  bool more = rem > 128;
+  if (kBounded) more = more && __shfl_sync(0xffffffffu, w[3], 31) <= hi;
+  if (more) {
+    load_step(p + 128, len - 128, rem >= 256, wn);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t hit = chunk_hit<kSorted>(ck, sorted_len, w[t]);
+      hits += hit;
+      if (kEmit) em.put(hit, w[t]);
+    }
+    p += 128;
+    len -= 128;
+    return false;
+  }
+  // ids ascend with 32 t + lane, so the ids taken (before end, at most hi)
+  // form a prefix of the step: stop at the first row of 32 with none
+  uint32_t taken = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const bool in = (int)len > 32 * t && (!kBounded || w[t] <= hi);
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (!m) break;
+    taken += __popc(m);
+    const uint32_t hit = (uint32_t)in & chunk_hit<kSorted>(ck, sorted_len, w[t]);
+    hits += hit;
+    if (kEmit) em.put(hit, w[t]);
+  }
+  // the new cursor follows the ids taken
+  out = (unsigned long long)(p - lane - arr) + taken;
+  return true;
+}
+
 template <bool kBounded, bool kSorted, bool kEmit>
 __device__ __forceinline__ unsigned long long stream_segment(
     const uint32_t* __restrict__ arr, const unsigned long long cur, const unsigned long long end,
@@ -706,43 +764,15 @@ __device__ __forceinline__ unsigned long long stream_segment(
   const uint32_t lane = lane_id();
   const uint32_t* p = arr + cur + lane;
   uint32_t len = (uint32_t)(end - cur) - lane;  // ids from p to end (as int: may be <= 0)
-  uint32_t w[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) w[t] = (int)len > 32 * t ? __ldg(p + 32 * t) : kEmpty;
+  uint32_t w[4], wn[4];
+  load_step(p, len, (int)(len + lane) >= 128, w);
+  unsigned long long out = end;
+  // two steps per iteration, w and wn trading roles (no register copies)
   for (;;) {
-    bool more = (int)(len + lane) > 128;
-    if (kBounded) more = more && __shfl_sync(0xffffffffu, w[3], 31) <= hi;
-    uint32_t wn[4];
-    if (more) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) wn[t] = (int)len > 128 + 32 * t ? __ldg(p + 128 + 32 * t) : kEmpty;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t hit = chunk_hit<kSorted>(ck, sorted_len, w[t]);
-        hits += hit;
-        if (kEmit) em.put(hit, w[t]);
-      }
-    } else {
-      // ids ascend with 32 t + lane, so the ids taken (before end, at most hi)
-      // form a prefix of the step: stop at the first row of 32 with none
-      uint32_t taken = 0;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const bool in = (int)len > 32 * t && (!kBounded || w[t] <= hi);
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (!m) break;
-        taken += __popc(m);
-        const uint32_t hit = (uint32_t)in & chunk_hit<kSorted>(ck, sorted_len, w[t]);
-        hits += hit;
-        if (kEmit) em.put(hit, w[t]);
-      }
-      // the new cursor follows the ids taken
-      return (unsigned long long)(p - lane - arr) + taken;
-    }
-    p += 128;
-    len -= 128;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) w[t] = wn[t];
+    if (segment_step<kBounded, kSorted, kEmit>(arr, p, len, w, wn, hi, ck, sorted_len, em, hits, out))
+      return out;
+    if (segment_step<kBounded, kSorted, kEmit>(arr, p, len, wn, w, hi, ck, sorted_len, em, hits, out))
+      return out;
   }
 }
 
@@ -814,6 +844,24 @@ __device__ __forceinline__ void fused_step(const uint32_t (&w)[4], int len, int 
 // taking a partial step of its own.  Same step structure as stream_segment.
 // A row holds fewer than n < 2^31 ids.
 template <bool kEmit>
+__device__ __forceinline__ bool fused_seg_step(const uint32_t*& p, uint32_t& len, const int rb,
+                                               const uint32_t (&w)[4], uint32_t (&wn)[4],
+                                               const Cuckoo ck, const Emit& em, uint32_t& c1,
+                                               uint32_t& c2c) {
+  const int rem = (int)(len + lane_id());  // ids from the step's first to end
+  const int q2 = rem - rb;                 // same-level ids from the step's first on
+  if (rem > 128) {
+    load_step(p + 128, len - 128, rem >= 256, wn);
+    fused_step<false, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
+    p += 128;
+    len -= 128;
+    return false;
+  }
+  fused_step<true, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
+  return true;
+}
+
+template <bool kEmit>
 __device__ __forceinline__ void stream_fused(const uint32_t* __restrict__ arr,
                                              unsigned long long cur, unsigned long long bnd,
                                              unsigned long long end, const Cuckoo ck,
@@ -823,25 +871,11 @@ __device__ __forceinline__ void stream_fused(const uint32_t* __restrict__ arr,
   const uint32_t* p = arr + cur + lane;
   uint32_t len = (uint32_t)(end - cur) - lane;  // ids from p to end (as int: may be <= 0)
   const int rb = (int)(end - bnd);              // ids of the other-level part
-  uint32_t w[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) w[t] = (int)len > 32 * t ? __ldg(p + 32 * t) : kEmpty;
+  uint32_t w[4], wn[4];
+  load_step(p, len, (int)(len + lane) >= 128, w);
   for (;;) {
-    const int rem = (int)(len + lane);  // ids from the step's first to end
-    const int q2 = rem - rb;            // same-level ids from the step's first on
-    if (rem > 128) {
-      uint32_t wn[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) wn[t] = (int)len > 128 + 32 * t ? __ldg(p + 128 + 32 * t) : kEmpty;
-      fused_step<false, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
-      p += 128;
-      len -= 128;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) w[t] = wn[t];
-    } else {
-      fused_step<true, kEmit>(w, (int)len, rem, q2, ck, em, c1, c2c);
-      return;
-    }
+    if (fused_seg_step<kEmit>(p, len, rb, w, wn, ck, em, c1, c2c)) return;
+    if (fused_seg_step<kEmit>(p, len, rb, wn, w, ck, em, c1, c2c)) return;
   }
 }
 
@@ -1013,10 +1047,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
         }
         EdgePass r;
         if (!sorted) {
-          if (bounded) {
-            r = stream_edge<true, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
-          } else if (kPlain || split) {
-            r = stream_edge<false, false, kEmit>(lcol, a, ae, b, be, hi_id, ck, entries, ed);
+          if (kPlain || split) {  // one segment: the part's own (plain pairs: [a, ae))
+            const bool seg1 = !kPlain && part;
+            const unsigned long long cur = seg1 ? b : a, end = seg1 ? be : ae;
+            uint32_t hits = 0;
+            const unsigned long long nc =
+                bounded ? stream_segment<true, false, kEmit>(lcol, cur, end, hi_id, ck, 0, ed, hits)
+                        : stream_segment<false, false, kEmit>(lcol, cur, end, hi_id, ck, 0, ed, hits);
+            r = seg1 ? EdgePass{a, nc, 0, hits} : EdgePass{nc, b, hits, 0};
           } else {  // one chunk: [b, be) and [a, ae) are adjacent (be == a)
             r = EdgePass{ae, be, 0, 0};
             stream_fused<kEmit>(lcol, b, be, ae, ck, ed, r.c1, r.c2c);
