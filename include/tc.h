@@ -236,7 +236,9 @@ typedef struct tc_params {
   uint32_t small_max_degree; /* cover edges with both degrees <= this use the direct merge */
   uint32_t hash_chunk;       /* owner-row entries per shared-memory hash chunk (multiple of 32,
                                 32..16384) */
-  uint32_t edges_per_item;   /* cover edges per hash work item (1..hash_block) */
+  uint32_t edges_per_item;   /* cover edges per hash work item: 1..1024 with hash_block 512,
+                                1..4096 with 1024; on graphs of 2^32 or more adjacency entries
+                                it is clamped to hash_block */
   uint32_t bfs_alpha;        /* top-down -> bottom-up when frontier edges > unexplored / alpha */
   uint32_t bfs_beta;         /* bottom-up -> top-down when frontier < n / beta */
   uint32_t sorted_lookup;    /* 1: look ids up by binary search in the sorted chunk instead of

@@ -5,11 +5,14 @@ The tunables change speed only, never the count:
 - ``medium_max_degree``: degree bound of the warp-merge bin;
 - ``hash_block``: threads per owner-hash block (512, or 1024 with one block per SM);
 - ``hash_chunk``: owner-row entries per shared-memory table;
-- ``edges_per_item``: cover edges per owner-hash work item;
+- ``edges_per_item``: cover edges per owner-hash work item (up to 2x a 512-thread block, 4x a
+  1024-thread one);
 - ``bfs_alpha`` / ``bfs_beta``: the direction switches of the BFS.
 
 ``tune`` runs a coordinate descent. It starts from the defaults and, one parameter at a time, tries
-each candidate value. A value is kept only if the measured total time drops by more than
+each candidate value. The block size, chunk and item length only pay off together (a 1024-thread
+block wants longer chunks and items than a 512-thread one), so one coordinate, ``shape``, moves the
+three at once through ``SHAPES`` before each is refined alone. A value is kept only if the measured total time drops by more than
 ``min_gain``. Every candidate's count must equal the default's. Times are the library's own
 CUDA-event totals (``ms_total`` of tc_stats), and the best of ``trials`` runs is kept.
 
@@ -35,15 +38,20 @@ CACHE = os.path.join(HERE, "tuned_params.json")
 
 GRID: Dict[str, Sequence[int]] = {
     "hash_block": (512, 1024),
-    "hash_chunk": (2048, 4096, 8192, 16384),
-    "edges_per_item": (64, 128, 256, 512, 1024),
+    "hash_chunk": (2048, 4096, 8192, 12288, 16384),
+    "edges_per_item": (64, 128, 256, 512, 1024, 2048, 4096),
     "small_max_degree": (0, 8, 16, 32, 64, 128, 256, 512, 1024),
     "medium_max_degree": (0, 128, 256, 512, 1024),
     "bfs_alpha": (4, 15, 40),
     "bfs_beta": (8, 18, 48),
 }
-ORDER = ("small_max_degree", "medium_max_degree", "hash_block", "hash_chunk", "edges_per_item",
-         "small_max_degree", "bfs_alpha", "bfs_beta")
+SHAPES = (
+    {"hash_block": 512, "hash_chunk": 8192, "edges_per_item": 1024},
+    {"hash_block": 1024, "hash_chunk": 12288, "edges_per_item": 4096},
+    {"hash_block": 1024, "hash_chunk": 16384, "edges_per_item": 1024},
+)
+ORDER = ("small_max_degree", "medium_max_degree", "shape", "hash_block", "hash_chunk",
+         "edges_per_item", "small_max_degree", "bfs_alpha", "bfs_beta")
 
 
 def signature(n: int, m: int, d_max: int, family: str = "", batch: int = 1) -> str:
@@ -66,10 +74,15 @@ def _measure(target, roots, params: dict, trials: int):
 
 
 def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials: int = 2,
-         min_gain: float = 0.02, time_budget_s: float = 120.0) -> dict:
-    """Coordinate descent over `grid` for a tc.Graph (roots: int) or tc.Batch (roots: list)."""
+         min_gain: float = 0.02, time_budget_s: float = 120.0,
+         shapes: Optional[Sequence[dict]] = None) -> dict:
+    """Coordinate descent over `grid` (and the joint `shapes`) for a tc.Graph (roots: int) or
+    tc.Batch (roots: list)."""
     from paper_2403_02997_gb300 import tc_params_default
-    grid = dict(GRID if grid is None else grid)
+    if grid is None:  # the default search includes the joint shapes
+        grid, shapes = dict(GRID), SHAPES if shapes is None else shapes
+    else:
+        grid, shapes = dict(grid), shapes or ()
     base = {k: v for k, v in tc_params_default().items()
             if k in ("small_max_degree", "medium_max_degree", "hash_block", "hash_chunk",
                      "edges_per_item", "bfs_alpha", "bfs_beta")}
@@ -78,13 +91,17 @@ def tune(target, roots, grid: Optional[Dict[str, Iterable[int]]] = None, trials:
     history = [{"params": dict(base), "ms": best_ms}]
     cur = dict(base)
     for name in ORDER:
-        if name not in grid or name not in cur:  # not a tunable of this library
+        if name == "shape":
+            moves = [dict(m) for m in shapes if set(m) <= set(cur)]
+        elif name not in grid or name not in cur:  # not a tunable of this library
             continue
-        for val in grid[name]:
-            if val == cur[name] or time.time() - t0 > time_budget_s:
+        else:
+            moves = [{name: int(v)} for v in grid[name]]
+        for mv in moves:
+            if all(cur[k] == v for k, v in mv.items()) or time.time() - t0 > time_budget_s:
                 continue
             cand = dict(cur)
-            cand[name] = int(val)
+            cand.update(mv)
             try:
                 ms, got = _measure(target, roots, cand, trials)
             except Exception as e:  # a value the library rejects is skipped
@@ -196,6 +213,9 @@ if __name__ == "__main__":
             roots = target.max_degree_vertex() if s.root == "maxdeg" else 0
             sig = signature(s.n, target.m, target.d_max, s.family)
         if args.fe and w != "batched":
+            tuned = lookup(sig, args.out)  # CETC-Seq as it runs: with its tuned parameters
+            if tuned:
+                target.set_params(**tuned)
             fe = learn_fe_threshold(target, roots, trials=args.trials)
             store_fe(sig, fe, args.out)
             print(json.dumps({"workload": w, "signature": sig, "fe": fe}), flush=True)

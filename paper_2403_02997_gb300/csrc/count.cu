@@ -923,7 +923,17 @@ __device__ __forceinline__ unsigned long long lower_bound_u32(const uint32_t* __
 // range (stream_fused).  Plain pairs (kPlain = true): the table is
 // tcol[tb[h], te[h]) and the streamer streams the one segment scol[sb[x],
 // se[x]); hits are tallied as c1, or as c2' when plain_as_c2 is set.
-template <int kThreads, bool kPlain, bool kEmit>
+// Edges per work item that the cursor arrays of k_owner_hash hold.  With
+// 32-bit positions (graphs of fewer than 2^32 adjacency entries) a cursor
+// takes half the shared memory of a 64-bit one, and the slices are longer:
+// fewer items, so fewer builds of each owner's tables.
+template <int kThreads, typename Pos>
+__host__ __device__ constexpr uint32_t owner_hash_cap() {
+  return sizeof(Pos) == 4 ? (kThreads == 2 * kHashBlock ? 4u : 2u) * (uint32_t)kThreads
+                          : (uint32_t)kThreads;
+}
+
+template <int kThreads, bool kPlain, bool kEmit, typename Pos = unsigned long long>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
     const HashRows rows, const unsigned long long* __restrict__ ooff,
     const uint32_t* __restrict__ ostream, const unsigned long long* __restrict__ ioff,
@@ -938,12 +948,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_owner_hash(
   const uint32_t* __restrict__ lcol = rows.scol;
   __shared__ unsigned long long s_item;
   __shared__ uint32_t s_next, s_fail;
-  // cursors of the slice's edges (edges_per_item <= kThreads)
-  __shared__ unsigned long long s_a[kThreads], s_ae[kThreads];
-  __shared__ unsigned long long s_b[kThreads], s_be[kThreads];
-  __shared__ uint32_t s_x[kEmit ? kThreads : 1];  // streamers (listing only)
+  // cursors of the slice's edges (positions in the rows: Pos holds nnz_cap)
+  constexpr uint32_t kCap = owner_hash_cap<kThreads, Pos>();
+  __shared__ Pos s_a[kCap], s_ae[kCap];
+  __shared__ Pos s_b[kCap], s_be[kCap];
+  __shared__ uint32_t s_x[kEmit ? kCap : 1];  // streamers (listing only)
   const unsigned lane = lane_id();
   Tally tl;
+  if (check_failed(per_item > kCap || (sizeof(Pos) == 4 && nnz_cap >= (1ull << 32)), ctr)) return;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctr->item_cursor, 1ull);
     __syncthreads();
@@ -1606,7 +1618,15 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   k_bucket<<<grid_for(nlarge, 256, sms * 16), 256, 0, st>>>(g->large, nlarge, g->ooff, g->ofill,
                                                            g->ostream, n, g->ctr); TC_LAUNCHED();
   const uint32_t chunk = g->params.hash_chunk;
-  const uint32_t per_item = g->params.edges_per_item;
+  const bool wide = g->params.hash_block == 2 * kHashBlock;
+  const int threads = wide ? 2 * kHashBlock : kHashBlock;
+  // 32-bit cursor positions when every position of the rows fits
+  const bool pos32 = g->nnz < (1ull << 32);
+  const uint32_t cap = wide ? (pos32 ? owner_hash_cap<2 * kHashBlock, uint32_t>()
+                                     : owner_hash_cap<2 * kHashBlock, unsigned long long>())
+                            : (pos32 ? owner_hash_cap<kHashBlock, uint32_t>()
+                                     : owner_hash_cap<kHashBlock, unsigned long long>());
+  const uint32_t per_item = g->params.edges_per_item < cap ? g->params.edges_per_item : cap;
   k_item_counts<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ocount, n, per_item, g->fdeg); TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   TC_TRY(exclusive_scan_u32(g->fdeg, g->ioff, n, g->scan, st));
@@ -1627,10 +1647,12 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   }
   k_item_owner<<<grid_for(n, 256, sms * 16), 256, 0, st>>>(g->ioff, n, g->item_owner); TC_LAUNCHED();
   const size_t smem = owner_hash_smem(chunk);
-  const bool wide = g->params.hash_block == 2 * kHashBlock;
-  const int threads = wide ? 2 * kHashBlock : kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, kPlain, kEmit>
-                          : (const void*)k_owner_hash<kHashBlock, kPlain, kEmit>;
+  using u64 = unsigned long long;
+  const void* kern =
+      wide ? (pos32 ? (const void*)k_owner_hash<2 * kHashBlock, kPlain, kEmit, uint32_t>
+                    : (const void*)k_owner_hash<2 * kHashBlock, kPlain, kEmit, u64>)
+           : (pos32 ? (const void*)k_owner_hash<kHashBlock, kPlain, kEmit, uint32_t>
+                    : (const void*)k_owner_hash<kHashBlock, kPlain, kEmit, u64>);
   TC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -1639,14 +1661,18 @@ tc_status run_owner_pass(tc_graph* g, unsigned long long nlarge, const HashRows&
   if (nitems < grid) grid = (unsigned)nitems;
   TC_CUDA_TRY(cudaEventRecord(g->ev[4], st));
   const uint32_t force_sorted = g->params.sorted_lookup ? 1u : 0u;
-  if (wide)
-    k_owner_hash<2 * kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
-        rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr, em, n, g->nnz);
+#define TC_OWNER_HASH_ARGS                                                                     \
+  rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,   \
+      plain_as_c2, voff, nb, gcount, g->ctr, em, n, g->nnz
+  if (wide && pos32)
+    k_owner_hash<2 * kHashBlock, kPlain, kEmit, uint32_t><<<grid, threads, smem, st>>>(TC_OWNER_HASH_ARGS);
+  else if (wide)
+    k_owner_hash<2 * kHashBlock, kPlain, kEmit, u64><<<grid, threads, smem, st>>>(TC_OWNER_HASH_ARGS);
+  else if (pos32)
+    k_owner_hash<kHashBlock, kPlain, kEmit, uint32_t><<<grid, threads, smem, st>>>(TC_OWNER_HASH_ARGS);
   else
-    k_owner_hash<kHashBlock, kPlain, kEmit><<<grid, threads, smem, st>>>(
-        rows, g->ooff, g->ostream, g->ioff, g->item_owner, nitems, chunk, per_item, force_sorted,
-        plain_as_c2, voff, nb, gcount, g->ctr, em, n, g->nnz);
+    k_owner_hash<kHashBlock, kPlain, kEmit, u64><<<grid, threads, smem, st>>>(TC_OWNER_HASH_ARGS);
+#undef TC_OWNER_HASH_ARGS
   TC_LAUNCHED();
   TC_CUDA_TRY(cudaGetLastError());
   return TC_OK;
@@ -1665,8 +1691,9 @@ tc_status scan_owners(tc_graph* g, cudaStream_t st, unsigned long long* nlarge) 
 
 tc_status owner_hash_fits(uint32_t chunk, uint32_t hash_block) {
   const bool wide = hash_block == 2 * kHashBlock;
-  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, false, false>
-                          : (const void*)k_owner_hash<kHashBlock, false, false>;
+  // the 32-bit-position instances hold the longer cursor arrays
+  const void* kern = wide ? (const void*)k_owner_hash<2 * kHashBlock, false, false, uint32_t>
+                          : (const void*)k_owner_hash<kHashBlock, false, false, uint32_t>;
   cudaFuncAttributes fa;
   TC_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
   int dev = 0, optin = 0;

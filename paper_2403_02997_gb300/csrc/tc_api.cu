@@ -200,7 +200,11 @@ tc_status tc_set_params(tc_graph* g, const tc_params* p) {
   const uint32_t c = p->hash_chunk;
   if (c < 32 || c > 16384 || c % 32 != 0) return TC_ERR_INVALID_ARG;
   if (p->hash_block != 512 && p->hash_block != 1024) return TC_ERR_INVALID_ARG;
-  if (p->edges_per_item == 0 || p->edges_per_item > p->hash_block || p->bfs_alpha == 0 ||
+  // edges per item: up to 2x (512-thread blocks) or 4x (1024) the block size
+  // (above the block size they are clamped to it on graphs of 2^32 or more
+  // adjacency entries, whose cursors take 64 bits)
+  if (p->edges_per_item == 0 || p->edges_per_item > (p->hash_block == 1024 ? 4096u : 1024u) ||
+      p->bfs_alpha == 0 ||
       p->bfs_beta == 0)
     return TC_ERR_INVALID_ARG;
   if (p->barrier_timeout_ms == 0 || p->barrier_timeout_ms > 600000) return TC_ERR_INVALID_ARG;

@@ -87,3 +87,25 @@ def test_fe_threshold_follows_the_faster_count(tmp_path):
     assert autotune.lookup_fe("missing", path) is None
     with pytest.raises(RuntimeError):                                    # counts must agree
         autotune.learn_fe_threshold(FakeGraph(10.0, 6.0, fwd_tri=8), 0, trials=1)
+
+
+class JointTarget(FakeTarget):
+    """Faster only with 1024-thread blocks, 12288-entry chunks and 4096-edge items together."""
+
+    def stats(self):
+        shape = (self.p.get("hash_block"), self.p.get("hash_chunk"), self.p.get("edges_per_item"))
+        return {"ms_total": 80.0 if shape == (1024, 12288, 4096) else 100.0 + (shape[0] == 1024)}
+
+
+def test_shape_move_reaches_a_joint_optimum(monkeypatch):
+    import paper_2403_02997_gb300 as tc
+    monkeypatch.setattr(tc, "tc_params_default",
+                        lambda: dict(small_max_degree=32, medium_max_degree=0, hash_block=512,
+                                     hash_chunk=8192, edges_per_item=512, bfs_alpha=15,
+                                     bfs_beta=18))
+    res = autotune.tune(JointTarget(), 0, trials=1)
+    p = res["params"]
+    assert (p["hash_block"], p["hash_chunk"], p["edges_per_item"]) == (1024, 12288, 4096)
+    # without the joint moves, single-coordinate steps never leave the default shape
+    res = autotune.tune(JointTarget(), 0, trials=1, grid=autotune.GRID)
+    assert res["params"]["hash_block"] == 512 and res["ms"] == 100.0

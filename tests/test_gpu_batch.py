@@ -59,7 +59,9 @@ def oracle_truth(items):
                                     dict(small_max_degree=1 << 30),
                                     dict(small_max_degree=8, medium_max_degree=256),
                                     dict(small_max_degree=0, hash_block=1024, hash_chunk=64,
-                                         edges_per_item=700)])
+                                         edges_per_item=700),
+                                    dict(small_max_degree=0, hash_block=1024, hash_chunk=96,
+                                         edges_per_item=3000)])
 def test_batch_counts_and_levels(params):
     items = mixed_graphs()
     want, roots, levels = oracle_truth(items)

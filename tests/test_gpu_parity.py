@@ -33,6 +33,10 @@ PARAMS = {
     "medium_only": dict(small_max_degree=0, medium_max_degree=1024, hash_chunk=64),
     "block1024": dict(small_max_degree=0, hash_block=1024, hash_chunk=16384, edges_per_item=1024),
     "block1024_tiny": dict(small_max_degree=0, hash_block=1024, hash_chunk=32, edges_per_item=5),
+    # items longer than the block (cursors held as 32-bit positions)
+    "items1024": dict(small_max_degree=0, hash_chunk=128, edges_per_item=1024),
+    "block1024_items4096": dict(small_max_degree=0, hash_block=1024, hash_chunk=256,
+                                edges_per_item=4096),
 }
 
 
@@ -180,6 +184,11 @@ def test_errors():
         g.set_params(hash_chunk=100)
     with pytest.raises(tc.TCError):
         g.set_params(hash_block=768)
+    with pytest.raises(tc.TCError):  # items of up to 2x a 512-thread block
+        g.set_params(edges_per_item=1025)
+    with pytest.raises(tc.TCError):  # and 4x a 1024-thread one
+        g.set_params(hash_block=1024, edges_per_item=4097)
+    g.set_params(hash_block=1024, edges_per_item=4096)
     assert g.count(2) == 0
     g.close()
 

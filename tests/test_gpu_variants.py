@@ -26,6 +26,7 @@ PARAMS = {
     "all_hash": dict(small_max_degree=0),
     "all_merge": dict(small_max_degree=1 << 30),
     "tiny_chunks": dict(small_max_degree=0, hash_chunk=32, edges_per_item=3),
+    "long_items": dict(small_max_degree=0, hash_block=1024, hash_chunk=128, edges_per_item=4096),
 }
 
 
