@@ -57,6 +57,9 @@ def parse_args():
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--no-tuned", action="store_true",
                    help="ignore the autotuner's table (paper_2403_02997_gb300/tuned_params.json)")
+    p.add_argument("--params", default="",
+                   help="JSON object of tc_params fields set after the tuned ones (single-graph "
+                        "workloads), e.g. to profile a small graph with the headline's settings")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle intersection work in the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -477,6 +480,8 @@ def run_ours(args, world, rank, local):
     from paper_2403_02997_gb300 import autotune
     tuned = None if args.no_tuned else autotune.lookup(
         autotune.signature(spec.n, g.m, g.d_max, spec.family))
+    if args.params:
+        tuned = dict(tuned or {}, **json.loads(args.params))
     if tuned:
         g.set_params(**tuned)
     params = tc.tc_params_default()
@@ -590,7 +595,7 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generator)",
         "config": dict(config_dict(spec, args), params=params,
-                       params_source="autotuned" if tuned else "defaults"),
+                       params_source=("--params" if args.params else "autotuned" if tuned else "defaults")),
         "triangles": T, "m": m, "num_cover": n_cover, "covering_ratio": n_cover / max(m, 1),
         "cover_intersections_per_s": n_cover / (statistics.mean(ms_inter) / 1e3)
         if statistics.mean(ms_inter) > 0 else None,

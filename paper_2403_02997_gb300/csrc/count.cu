@@ -187,8 +187,8 @@ struct Emit {
 };
 
 // Cover edges, compacted: k_cover queues the cover edges its lanes find (ballot
-// ranks into a per-warp shared-memory queue) and, once 32 are queued, every
-// lane bins one of them (bin_cover: its rows' offsets, then the small-bin
+// ranks into a per-warp shared-memory queue) and, once 32 are queued, appends
+// them to the cover list with one atomic and every lane bins one of them (bin_cover: its rows' offsets, then the small-bin
 // merge or an append).  Without the queue only the lanes whose entry happened
 // to be a cover edge -- about a quarter of them -- would do that work while
 // the rest of the warp waited.  In batch mode the hits go to u's graph.
@@ -258,9 +258,14 @@ __device__ __forceinline__ void bin_cover(bool valid, uint2 e,
       is_large = true;
       const bool v_owns = dv > du || (dv == du && v > u);
       le = v_owns ? make_uint2(v, u) : make_uint2(u, v);
-      atomicAdd(&ocount[le.x], 1u);
     }
   }
+  // the lanes with one owner (queued edges often share a hub) add to its
+  // count with one atomic
+  const uint32_t key = is_large ? le.x : kEmpty;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (is_large && lane_id() == (unsigned)__ffs(peers) - 1)
+    atomicAdd(&ocount[le.x], (uint32_t)__popc(peers));
   warp_append_pair(is_medium, e, medium, &ctr->num_medium);
   warp_append_pair(is_large, le, large, &ctr->num_large);
 }
@@ -353,8 +358,8 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
           }
         }
       }
-      warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
       if (kEmit) {
+        warp_append_pair(is_cover, ce, cover, &ctr->num_cover);
         warp_append_pair(is_medium, ce, medium, &ctr->num_medium);
         warp_append_pair(is_large, le, large, &ctr->num_large);
       } else {
@@ -362,9 +367,11 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
         const unsigned m = __ballot_sync(0xffffffffu, is_cover);
         if (is_cover) q[qn + __popc(m & ((1u << lane) - 1u))] = ce;
         qn += __popc(m);
-        if (qn >= kWarp) {  // every lane bins one queued cover edge
+        if (qn >= kWarp) {  // every lane bins one queued cover edge (and lists it)
           __syncwarp();
-          bin_cover(true, q[lane], row_ptr, col, level, small_max, medium_max, ocount, medium,
+          const uint2 qe = q[lane];
+          warp_append_pair(true, qe, cover, &ctr->num_cover);
+          bin_cover(true, qe, row_ptr, col, level, small_max, medium_max, ocount, medium,
                     large, ctr, voff, nb, gcount, tl, run);
           __syncwarp();
           if (lane < qn - kWarp) q[lane] = q[kWarp + lane];
@@ -377,8 +384,10 @@ __global__ void __launch_bounds__(kCoverBlock) k_cover(const unsigned long long*
   if (!kEmit) {
     __syncwarp();
     const unsigned lane = lane_id();
-    bin_cover(lane < qn, lane < qn ? q[lane] : make_uint2(0, 0), row_ptr, col, level, small_max,
-              medium_max, ocount, medium, large, ctr, voff, nb, gcount, tl, run);
+    const uint2 qe = lane < qn ? q[lane] : make_uint2(0, 0);
+    warp_append_pair(lane < qn, qe, cover, &ctr->num_cover);
+    bin_cover(lane < qn, qe, row_ptr, col, level, small_max, medium_max, ocount, medium, large,
+              ctr, voff, nb, gcount, tl, run);
   }
   if (nb) run.flush(gcount);
   flush_tally(tl, ctr);
@@ -454,7 +463,8 @@ __global__ void __launch_bounds__(kWarpMergeBlock) k_warp_merge(
 
 // One warp per row of degree <= kSplitMax (grid-stride).  Pass 1 counts the
 // neighbours on another level; pass 2 writes both parts in order with ballot
-// ranks, the same-level part first.  lsplit[x] is where the other-level part
+// ranks, the same-level part first (rows of up to 128 entries in one pass,
+// their ids and level tests held in registers).  lsplit[x] is where the other-level part
 // starts.  Longer rows are left to the tile kernels below.
 __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
                               const uint32_t* __restrict__ col, const int32_t* __restrict__ level,
@@ -471,6 +481,31 @@ __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
       continue;
     }
     const int32_t lx = level[x];
+    if (e - b <= 128) {  // one pass: the row's ids and level tests stay in registers
+      uint32_t w[4];
+      unsigned mo[4], ms[4];
+      unsigned long long other = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const unsigned long long j = b + 32 * t + lane;
+        const bool valid = j < e;
+        w[t] = valid ? col[j] : 0u;
+        const bool o = valid && level[w[t]] != lx;
+        mo[t] = __ballot_sync(0xffffffffu, o);
+        ms[t] = __ballot_sync(0xffffffffu, valid && !o);
+        other += __popc(mo[t]);
+      }
+      unsigned long long ps = b, po = e - other;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (mo[t] & (1u << lane)) lcol[po + __popc(mo[t] & lt)] = w[t];
+        else if (ms[t] & (1u << lane)) lcol[ps + __popc(ms[t] & lt)] = w[t];
+        po += __popc(mo[t]);
+        ps += __popc(ms[t]);
+      }
+      if (lane == 0) lsplit[x] = e - other;
+      continue;
+    }
     unsigned long long other = 0;
     for (unsigned long long j0 = b; j0 < e; j0 += 32) {
       const unsigned long long j = j0 + lane;
@@ -592,11 +627,25 @@ __global__ void __launch_bounds__(kTileBlock) k_split_tile_write(
 __global__ void k_bucket(const uint2* __restrict__ large, unsigned long long count,
                          const unsigned long long* __restrict__ ooff, uint32_t* __restrict__ ofill,
                          uint32_t* __restrict__ ostream, uint32_t n, DevCounters* ctr) {
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint2 e = large[i];
-    if (check_failed(e.x >= n, ctr)) continue;
-    const unsigned long long pos = ooff[e.x] + atomicAdd(&ofill[e.x], 1u);
+  // the lanes of a warp holding pairs of one owner (consecutive pairs often
+  // share it: the cover scan emits a row's entries together) take their slots
+  // with one atomic
+  const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;  // multiple of 32
+  for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+       i0 < count; i0 += stride) {
+    const unsigned long long i = i0 + lane;
+    uint2 e = make_uint2(kEmpty, 0u);
+    if (i < count) e = large[i];
+    const bool ok = i < count && !check_failed(e.x >= n, ctr);
+    const uint32_t key = ok ? e.x : kEmpty;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const unsigned leader = __ffs(peers) - 1;
+    uint32_t start = 0;
+    if (ok && lane == leader) start = atomicAdd(&ofill[e.x], (uint32_t)__popc(peers));
+    start = __shfl_sync(0xffffffffu, start, leader);
+    if (!ok) continue;
+    const unsigned long long pos = ooff[e.x] + start + __popc(peers & lt);
     if (check_failed(pos >= count || pos >= ooff[e.x + 1], ctr)) continue;
     ostream[pos] = e.y;
   }
