@@ -461,77 +461,119 @@ __global__ void __launch_bounds__(kWarpMergeBlock) k_warp_merge(
   flush_tally(tl, ctr);
 }
 
-// One warp per row of degree <= kSplitMax (grid-stride).  Pass 1 counts the
-// neighbours on another level; pass 2 writes both parts in order with ballot
-// ranks, the same-level part first (rows of up to 128 entries in one pass,
-// their ids and level tests held in registers).  lsplit[x] is where the other-level part
-// starts.  Longer rows are left to the tile kernels below.
+// The level split of one row x = [b, e) (kSplitMax >= e - b > 0) by the whole
+// warp: pass 1 counts the neighbours on another level, pass 2 writes both
+// parts in order with ballot ranks, the same-level part first (rows of up to
+// 128 entries in one pass, their ids and level tests held in registers).
+__device__ __forceinline__ void split_row_warp(const uint32_t* __restrict__ col,
+                                               const int32_t* __restrict__ level,
+                                               unsigned long long b, unsigned long long e,
+                                               int32_t lx, uint32_t* __restrict__ lcol,
+                                               unsigned long long* lsplit_x) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  if (e - b <= 128) {
+    uint32_t w[4];
+    unsigned mo[4], ms[4];
+    unsigned long long other = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const unsigned long long j = b + 32 * t + lane;
+      const bool valid = j < e;
+      w[t] = valid ? col[j] : 0u;
+      const bool o = valid && level[w[t]] != lx;
+      mo[t] = __ballot_sync(0xffffffffu, o);
+      ms[t] = __ballot_sync(0xffffffffu, valid && !o);
+      other += __popc(mo[t]);
+    }
+    unsigned long long ps = b, po = e - other;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (mo[t] & (1u << lane)) lcol[po + __popc(mo[t] & lt)] = w[t];
+      else if (ms[t] & (1u << lane)) lcol[ps + __popc(ms[t] & lt)] = w[t];
+      po += __popc(mo[t]);
+      ps += __popc(ms[t]);
+    }
+    if (lane == 0) *lsplit_x = e - other;
+    return;
+  }
+  unsigned long long other = 0;
+  for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+    const unsigned long long j = j0 + lane;
+    const bool o = j < e && level[col[j]] != lx;
+    other += __popc(__ballot_sync(0xffffffffu, o));
+  }
+  unsigned long long ps = b, po = e - other;
+  for (unsigned long long j0 = b; j0 < e; j0 += 32) {
+    const unsigned long long j = j0 + lane;
+    uint32_t w = 0;
+    const bool valid = j < e;
+    bool o = false;
+    if (valid) {
+      w = col[j];
+      o = level[w] != lx;
+    }
+    const unsigned mo = __ballot_sync(0xffffffffu, valid && o);
+    const unsigned ms = __ballot_sync(0xffffffffu, valid && !o);
+    if (valid) {
+      if (o) lcol[po + __popc(mo & lt)] = w;
+      else lcol[ps + __popc(ms & lt)] = w;
+    }
+    po += __popc(mo);
+    ps += __popc(ms);
+  }
+  if (lane == 0) *lsplit_x = e - other;
+}
+
+// Level split of the rows of degree <= kSplitMax: per row x a copy of N(x) as
+// [same-level part | other-level part], each ascending; lsplit[x] is where the
+// other-level part starts.  A warp takes 32 consecutive rows (grid-stride):
+// a row of at most kLaneRow entries goes to its own lane (ids and level tests
+// in registers, so many short rows have their loads in flight together), the
+// longer ones to the whole warp, one after another.  Rows longer than
+// kSplitMax are left to the tile kernels below.
+constexpr uint32_t kLaneRow = 16;
+
 __global__ void k_level_split(const unsigned long long* __restrict__ row_ptr,
                               const uint32_t* __restrict__ col, const int32_t* __restrict__ level,
                               uint32_t n, uint32_t* __restrict__ lcol,
                               unsigned long long* __restrict__ lsplit) {
   const unsigned lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  const uint64_t warps = (uint64_t)gridDim.x * blockDim.x / 32;
-  for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; x < n; x += warps) {
-    const unsigned long long b = row_ptr[x], e = row_ptr[x + 1];
-    if (e - b > kSplitMax) continue;
-    if (e == b) {
-      if (lane == 0) lsplit[x] = b;
-      continue;
-    }
-    const int32_t lx = level[x];
-    if (e - b <= 128) {  // one pass: the row's ids and level tests stay in registers
-      uint32_t w[4];
-      unsigned mo[4], ms[4];
-      unsigned long long other = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // rows per sweep (32 per warp)
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); x0 < n;
+       x0 += stride) {
+    const uint64_t x = x0 + lane;
+    const bool valid = x < n;
+    const unsigned long long b = valid ? row_ptr[x] : 0, e = valid ? row_ptr[x + 1] : 0;
+    const unsigned long long d = e - b;
+    const int32_t lx = valid && d ? level[x] : 0;
+    if (valid && d <= kLaneRow) {  // this lane's row
+      uint32_t w[kLaneRow];
+      uint32_t obits = 0;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const unsigned long long j = b + 32 * t + lane;
-        const bool valid = j < e;
-        w[t] = valid ? col[j] : 0u;
-        const bool o = valid && level[w[t]] != lx;
-        mo[t] = __ballot_sync(0xffffffffu, o);
-        ms[t] = __ballot_sync(0xffffffffu, valid && !o);
-        other += __popc(mo[t]);
-      }
+      for (uint32_t i = 0; i < kLaneRow; ++i) w[i] = i < d ? col[b + i] : 0u;
+#pragma unroll
+      for (uint32_t i = 0; i < kLaneRow; ++i)
+        if (i < d && level[w[i]] != lx) obits |= 1u << i;
+      const uint32_t other = __popc(obits);
       unsigned long long ps = b, po = e - other;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (mo[t] & (1u << lane)) lcol[po + __popc(mo[t] & lt)] = w[t];
-        else if (ms[t] & (1u << lane)) lcol[ps + __popc(ms[t] & lt)] = w[t];
-        po += __popc(mo[t]);
-        ps += __popc(ms[t]);
+      for (uint32_t i = 0; i < kLaneRow; ++i) {
+        if (i >= d) break;
+        if (obits & (1u << i)) lcol[po++] = w[i];
+        else lcol[ps++] = w[i];
       }
-      if (lane == 0) lsplit[x] = e - other;
-      continue;
+      lsplit[x] = e - other;
     }
-    unsigned long long other = 0;
-    for (unsigned long long j0 = b; j0 < e; j0 += 32) {
-      const unsigned long long j = j0 + lane;
-      const bool o = j < e && level[col[j]] != lx;
-      other += __popc(__ballot_sync(0xffffffffu, o));
+    unsigned long_rows = __ballot_sync(0xffffffffu, valid && d > kLaneRow && d <= kSplitMax);
+    while (long_rows) {  // warp-uniform
+      const unsigned l = __ffs(long_rows) - 1;
+      long_rows &= long_rows - 1;
+      const unsigned long long rb = __shfl_sync(0xffffffffu, b, l);
+      const unsigned long long re = __shfl_sync(0xffffffffu, e, l);
+      const int32_t rl = __shfl_sync(0xffffffffu, lx, l);
+      split_row_warp(col, level, rb, re, rl, lcol, &lsplit[x0 + l]);
     }
-    unsigned long long ps = b, po = e - other;
-    for (unsigned long long j0 = b; j0 < e; j0 += 32) {
-      const unsigned long long j = j0 + lane;
-      uint32_t w = 0;
-      const bool valid = j < e;
-      bool o = false;
-      if (valid) {
-        w = col[j];
-        o = level[w] != lx;
-      }
-      const unsigned mo = __ballot_sync(0xffffffffu, valid && o);
-      const unsigned ms = __ballot_sync(0xffffffffu, valid && !o);
-      if (valid) {
-        if (o) lcol[po + __popc(mo & lt)] = w;
-        else lcol[ps + __popc(ms & lt)] = w;
-      }
-      po += __popc(mo);
-      ps += __popc(ms);
-    }
-    if (lane == 0) lsplit[x] = e - other;
   }
 }
 
