@@ -569,6 +569,8 @@ def run_ours(args, world, rank, local):
     for _ in range(max(e2e_steps, 1) if e2e_steps else 0):
         gh = tc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), spec.n,
                       stream=stream)
+        if tuned:  # the parameters the device-resident count ran with
+            gh.set_params(**tuned)
         r = gh.max_degree_vertex() if spec.root == "maxdeg" else 0
         c = gh.count(r, stream=stream)
         gh.close()

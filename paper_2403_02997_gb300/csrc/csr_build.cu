@@ -80,7 +80,7 @@ __global__ void k_make_keys_multi(const uint32_t* __restrict__ src, const uint32
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortBlock = 256;  // == kRadix: one digit owner per thread
-constexpr int kSortItems = 32;
+constexpr int kSortItems = 16;  // 4096 keys (32 KB) per tile: 16 keys per digit on average
 constexpr uint64_t kSortTile = (uint64_t)kSortBlock * kSortItems;
 constexpr int kSortWarps = kSortBlock / 32;
 static_assert(kSortBlock == kRadix, "digit ownership assumes one thread per digit");
@@ -101,28 +101,47 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(const unsigned long l
   hist[(uint64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Stable scatter.  Keys are taken in rounds of kSortBlock (round r, thread t
-// holds key r*kSortBlock + t: index order) and ranked within a round by
-// (warp, lane), so equal digits keep their input order.  Thread d owns digit d:
-// it turns the per-warp counts of the round into absolute output positions and
-// advances the digit's running offset.
+// Stable scatter, staged through shared memory so that the writes to each
+// digit's output range go out as contiguous runs (about kSortTile / kRadix
+// keys per digit and tile) instead of one scattered 8-byte write per key.
+// The tile's keys are first ranked by digit in index order: they are taken in
+// rounds of kSortBlock (round r, thread t holds key r*kSortBlock + t) and
+// ranked within a round by (warp, lane), so equal digits keep their input
+// order; thread d owns digit d and turns the per-warp counts of the round
+// into positions in the tile's digit-sorted copy in shared memory.  Then the
+// copy is written out in order, key p of the copy (digit d) to the digit's
+// global offset for this tile plus p minus the digit's start in the copy.
 __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned long long* __restrict__ in,
                                                               unsigned long long* __restrict__ out,
                                                               uint64_t N, int shift, uint32_t nb,
                                                               const unsigned long long* __restrict__ offs) {
+  extern __shared__ unsigned long long s_keys[];  // kSortTile keys, digit-sorted
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
-  __shared__ unsigned long long pos[kSortWarps][kRadix];
+  __shared__ uint32_t pos[kSortWarps][kRadix];
+  __shared__ uint32_t s_start[kRadix];             // digit d's first position in s_keys
+  __shared__ unsigned long long s_goff[kRadix];    // digit d's first output position
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5, dd = threadIdx.x;
-  unsigned long long run_off = offs[(uint64_t)dd * nb + blockIdx.x];
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+  const uint32_t tile_n = (uint32_t)(N - base < kSortTile ? N - base : kSortTile);
+  // the tile's digit counts are the steps of the histogram's scan (digit-
+  // major, tile-minor: the entry after (d, tile) is the next one in the
+  // scan's order, the total at the end), and their scan gives s_start
+  __shared__ uint32_t s_tmp[kSortWarps + 1];
+  const uint64_t hi = (uint64_t)dd * nb + blockIdx.x;
+  const unsigned long long g0 = offs[hi];
+  s_goff[dd] = g0;
+  const uint32_t cnt = (uint32_t)(offs[hi + 1] - g0);
+  uint32_t total = 0;
+  s_start[dd] = block_exclusive_scan(cnt, s_tmp, &total);
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][dd] = 0;
   __syncthreads();
+  uint32_t run_off = s_start[dd];
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
   for (int r = 0; r < kSortItems; ++r) {
-    const uint64_t i = base + (uint64_t)r * kSortBlock + threadIdx.x;
-    const bool valid = i < N;
-    const unsigned long long key = valid ? in[i] : 0ull;
+    const uint32_t i = (uint32_t)r * kSortBlock + threadIdx.x;
+    const bool valid = i < tile_n;
+    const unsigned long long key = valid ? in[base + i] : 0ull;
     const unsigned d = valid ? ((unsigned)(key >> shift) & (kRadix - 1)) : (unsigned)kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const unsigned lower = __popc(peers & lt_mask);
@@ -130,14 +149,27 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const unsigned lon
     __syncthreads();
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
-      unsigned c = wcnt[w][dd];
+      const uint32_t c = wcnt[w][dd];
       wcnt[w][dd] = 0;
       pos[w][dd] = run_off;
       run_off += c;
     }
     __syncthreads();
-    if (valid) out[pos[warp][d] + lower] = key;
+    if (valid) s_keys[pos[warp][d] + lower] = key;
   }
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < tile_n; p += kSortBlock) {
+    const unsigned long long key = s_keys[p];
+    const unsigned d = (unsigned)(key >> shift) & (kRadix - 1);
+    out[s_goff[d] + (p - s_start[d])] = key;
+  }
+}
+
+// The scatter's static plus dynamic shared memory is above the 48 KB a launch
+// gets without opting in.
+cudaError_t radix_scatter_smem() {
+  return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kSortTile * sizeof(unsigned long long)));
 }
 
 constexpr int kDedupBlock = 512;
@@ -261,11 +293,12 @@ tc_status sort_keys(unsigned long long** keys, unsigned long long** tmp, uint64_
       cudaMalloc(&hoff, sizeof(unsigned long long) * (hcount + 1)) != cudaSuccess ||
       cudaMalloc(&ss.sums, sizeof(unsigned long long) * ss.capacity) != cudaSuccess)
     status = TC_ERR_OOM;
+  if (status == TC_OK && radix_scatter_smem() != cudaSuccess) status = TC_ERR_CUDA;
   for (int shift = 0; shift < bits && status == TC_OK; shift += kRadixBits) {
     k_radix_hist<<<(unsigned)nb, kSortBlock, 0, st>>>(*keys, N, shift, (uint32_t)nb, hist); TC_LAUNCHED();
     status = exclusive_scan_u32(hist, hoff, hcount, ss, st);
     if (status != TC_OK) break;
-    k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, st>>>(*keys, *tmp, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
+    k_radix_scatter<<<(unsigned)nb, kSortBlock, kSortTile * sizeof(unsigned long long), st>>>(*keys, *tmp, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
     unsigned long long* t = *keys;
     *keys = *tmp;
     *tmp = t;
@@ -322,10 +355,11 @@ tc_status build_csr(tc_graph* g, const uint32_t* d_src, const uint32_t* d_dst, u
                                                                reinterpret_cast<ulonglong2*>(keys_a),
                                                                g->ctr);
       TC_LAUNCHED();
+      if (radix_scatter_smem() != cudaSuccess) fail(TC_ERR_CUDA);
       for (int shift = 0; shift < 2 * kb && status == TC_OK; shift += kRadixBits) {
         k_radix_hist<<<(unsigned)nb, kSortBlock, 0, st>>>(keys_a, N, shift, (uint32_t)nb, hist); TC_LAUNCHED();
         if (exclusive_scan_u32(hist, hoff, hcount, ss, st) != TC_OK) { fail(TC_ERR_CUDA); break; }
-        k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, st>>>(keys_a, keys_b, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
+        k_radix_scatter<<<(unsigned)nb, kSortBlock, kSortTile * sizeof(unsigned long long), st>>>(keys_a, keys_b, N, shift, (uint32_t)nb, hoff); TC_LAUNCHED();
         unsigned long long* t = keys_a;
         keys_a = keys_b;
         keys_b = t;
