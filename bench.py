@@ -566,15 +566,22 @@ def run_ours(args, world, rank, local):
     e2e_steps = args.e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_parts = {"create": [], "count": [], "close": []}
     for _ in range(max(e2e_steps, 1) if e2e_steps else 0):
+        ta = time.perf_counter()
         gh = tc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), spec.n,
                       stream=stream)
         if tuned:  # the parameters the device-resident count ran with
             gh.set_params(**tuned)
         r = gh.max_degree_vertex() if spec.root == "maxdeg" else 0
+        tb = time.perf_counter()
         c = gh.count(r, stream=stream)
+        tc_ = time.perf_counter()
         gh.close()
+        td = time.perf_counter()
         assert c == T
+        for k, v in (("create", tb - ta), ("count", tc_ - tb), ("close", td - tc_)):
+            e2e_parts[k].append(v)
     if e2e_steps:
         t_e2e = (time.perf_counter() - t0) / e2e_steps
         e2e_max = max_over_ranks(t_e2e, world)
@@ -621,7 +628,10 @@ def run_ours(args, world, rank, local):
                    "what": "tc_graph_create from device-resident edge lists: key build, radix "
                            "sort, dedup, CSR (allocation included)"},
         "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 8 * E,
-                "d2h_bytes_per_step": 8, "seconds_per_step": e2e_max},
+                "d2h_bytes_per_step": 8, "seconds_per_step": e2e_max,
+                "parts_ms": {k: [round(x * 1e3, 1) for x in v] for k, v in e2e_parts.items()},
+                "what": "host edge lists (pinned) -> tc_graph_create (H2D + CSR build) -> "
+                        "tc_count -> tc_graph_destroy"},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
