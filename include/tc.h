@@ -64,7 +64,8 @@ typedef enum tc_status {
  * Errors: TC_ERR_INVALID_ARG (out == NULL, or num_edges > 0 with a NULL array,
  * or num_vertices >= 2^31), TC_ERR_VERTEX_RANGE (an id >= num_vertices; *out
  * stays NULL), TC_ERR_OOM, TC_ERR_CUDA.  num_vertices == 0 or num_edges == 0 is
- * valid and gives an edgeless graph.  The handle owns all its device memory.
+ * valid and gives an edgeless graph.  The handle owns all its device memory,
+ * taken stream-ordered from the library's memory pool (see tc_pool_trim).
  */
 tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num_edges,
                           uint32_t num_vertices, int edges_on_device, void* stream,
@@ -88,8 +89,9 @@ tc_status tc_graph_relabel_degree(const tc_graph* g, void* stream, tc_graph** ou
 /*
  * Free the handle and all device memory it owns.  NULL is accepted.  Every
  * call on a handle has finished its device work when it returns (each
- * synchronises its own stream), so destroy adds no synchronisation of its own
- * (cudaFree itself waits for the device).
+ * synchronises its own stream), so destroy adds no synchronisation of its own.
+ * The memory goes back to the library's pool (reserved for the next handle
+ * until tc_pool_trim).
  */
 tc_status tc_graph_destroy(tc_graph* g);
 
@@ -327,7 +329,7 @@ tc_status tc_batch_destroy(tc_batch* b);
 
 /*
  * The library's memory pool on the current device (stream-ordered memory of
- * the batches built from edge lists).  tc_pool_trim releases reserved but
+ * the graphs from tc_graph_create and the batches built from edge lists).  tc_pool_trim releases reserved but
  * unused memory until at most keep_bytes stay reserved (it synchronises the
  * library's free stream first); tc_pool_reserved reports the bytes the pool
  * holds from the driver now.  Errors: TC_ERR_INVALID_ARG (NULL), TC_ERR_CUDA.

@@ -226,6 +226,10 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tc_graph* g = new (std::nothrow) tc_graph();
   if (!g) return TC_ERR_OOM;
+  // device memory comes stream-ordered from the library's pool: a graph built
+  // after another was destroyed reuses its memory without mapping new pages,
+  // and destroying one does not wait for the whole device
+  g->pooled = true;
   params_default(&g->params);
   std::memset(&g->stats, 0, sizeof(g->stats));
   g->n = num_vertices;
@@ -234,7 +238,9 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
   uint32_t* staged_dst = nullptr;
   do {
     if ((s = dalloc(g, &g->ctr, 1, st)) != TC_OK) break;
-    if (cudaMallocHost(reinterpret_cast<void**>(&g->ctr_host), sizeof(DevCounters)) != cudaSuccess) {
+    // pageable: freeing pinned memory would synchronise the device
+    g->ctr_host = new (std::nothrow) DevCounters();
+    if (!g->ctr_host) {
       s = TC_ERR_OOM;
       break;
     }
@@ -259,12 +265,11 @@ tc_status tc_graph_create(const uint32_t* src, const uint32_t* dst, uint64_t num
     if ((s = alloc_count_state(g, st)) != TC_OK) break;
     s = sync_status(g, st);
   } while (0);
-  if (staged_src || staged_dst) {
-    cudaStreamSynchronize(st);
-    if (staged_src) cudaFree(staged_src);
-    if (staged_dst) cudaFree(staged_dst);
-  }
+  // the staging buffers go back to the pool after the build that read them
+  dev_free(g, staged_src, st);
+  dev_free(g, staged_dst, st);
   if (s != TC_OK) {
+    cudaStreamSynchronize(st);  // nothing of the failed build may still use the memory
     free_graph(g);
     return s;
   }
