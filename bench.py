@@ -520,15 +520,6 @@ def run_ours(args, world, rank, local):
     total_edges = sum_over_ranks(float(m) * args.steps, world)
     value = total_edges / (max_ms / 1000.0)
 
-    # roofline of the dominant kernel (owner-hash intersection), algorithmic bytes
-    rp, col = g.csr()
-    cu, cv = g.cover_edges()
-    hb = hash_kernel_bytes(rp, col, g.levels(), cu, cv, params)
-    deg = np.diff(rp.astype(np.int64))
-    survey_bytes = int(24 * m + 12 * spec.n + 16 * n_cover +
-                       4 * (deg[cu].sum() + deg[cv].sum()) + 4 * (st["c1"] + st["c2"]))
-    del rp, col, cu, cv, deg
-
     # the paper's variants on the same graph and root (same count; not the headline)
     variants = {}
     for name, fn in (("cetc_seq_s", lambda: g.count_split(root, stream=stream)),
@@ -556,12 +547,6 @@ def run_ours(args, world, rank, local):
             "threshold": fe_thr, "covering_ratio": n_cover / max(m, 1),
             "ran": "forward" if fe_forward else "cetc_seq", "ms": statistics.median(ms),
             "edges_per_s": m / (statistics.median(ms) / 1e3)}
-    peak, peak_kind = measured_peaks()
-    hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
-    achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0
-    traffic, traffic_stale = profiled_traffic(args.workload)
-    dram_rate = traffic / (hash_ms / 1e3) / 1e9 if traffic and hash_ms > 0 else None
-
     # end to end through the C ABI from pinned host buffers
     e2e_steps = args.e2e_steps
     e2e_parts = {"create": [], "count": [], "close": []}
@@ -591,6 +576,24 @@ def run_ours(args, world, rank, local):
         e2e_value = sum_over_ranks(float(m), world) / e2e_max
     else:  # profiling runs skip the end-to-end leg
         e2e_max, e2e_value = None, None
+
+    # roofline of the dominant kernel (owner-hash intersection), algorithmic bytes.  The host-side
+    # byte model allocates and frees many GB of host memory, which slows the driver's calls for a
+    # while afterwards, so it runs after the end-to-end leg; the levels and cover set are those of
+    # a CETC-Seq count (the variants above may have run the forward count last).
+    assert g.count(root, stream=stream) == T
+    rp, col = g.csr()
+    cu, cv = g.cover_edges()
+    hb = hash_kernel_bytes(rp, col, g.levels(), cu, cv, params)
+    deg = np.diff(rp.astype(np.int64))
+    survey_bytes = int(24 * m + 12 * spec.n + 16 * n_cover +
+                       4 * (deg[cu].sum() + deg[cv].sum()) + 4 * (st["c1"] + st["c2"]))
+    del rp, col, cu, cv, deg
+    peak, peak_kind = measured_peaks()
+    hash_ms = statistics.mean(ms_hash) if ms_hash else 0.0
+    achieved = hb["bytes"] / (hash_ms / 1e3) / 1e9 if hash_ms > 0 else 0.0
+    traffic, traffic_stale = profiled_traffic(args.workload)
+    dram_rate = traffic / (hash_ms / 1e3) / 1e9 if traffic and hash_ms > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
