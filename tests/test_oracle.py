@@ -446,6 +446,15 @@ def test_split_disconnected():
 # Degree ordering (Algorithms CETC-Seq-D / CETC-Seq-SD)
 # --------------------------------------------------------------------------
 
+def test_degree_order_worked_example():
+    """A 4-cycle 0-1-2-3 with the chord 0-2: degrees 3, 2, 3, 2, so by decreasing degree
+    and then increasing id the order is 0, 2, 1, 3 (worked by hand)."""
+    s = np.array([0, 1, 2, 3, 0], np.uint32)
+    d = np.array([1, 2, 3, 0, 2], np.uint32)
+    rp, _ = oracle.build_csr(4, s, d)
+    assert oracle.degree_order(rp).tolist() == [0, 2, 1, 3]
+
+
 @pytest.mark.parametrize("family,seed", [("er", 3), ("rmat", 7), ("wheel", 0), ("union", 1)])
 def test_degree_order(family, seed):
     if family == "er":
@@ -465,6 +474,9 @@ def test_degree_order(family, seed):
     # the definition, restated with Python's sort
     assert order.tolist() == sorted(range(n), key=lambda v: (-int(deg[v]), v))
     assert np.all(np.diff(deg[order]) <= 0)
+    # ties: among vertices of one degree the ids ascend
+    tie = deg[order][:-1] == deg[order][1:]
+    assert np.all(order[:-1][tie] < order[1:][tie])
     s2, d2 = oracle.relabel_edges(order, s, d)
     rp2, col2 = oracle.build_csr(n, s2, d2)
     assert np.array_equal(np.diff(rp2), deg[order])
