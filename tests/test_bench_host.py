@@ -57,3 +57,41 @@ def test_reference_arm_line():
     assert line["est_full_seconds"] > 0 and line["ms_per_step"] > 0
     assert abs(line["value"] - line["cpu_baseline"]["value"]) <= 1e-9 * line["value"]
     assert {"seq", "omp"} <= set(line["cpu_baseline"])
+
+
+def test_hash_kernel_bytes_against_brute_force():
+    """The roofline's algorithmic-byte model of the owner-hash kernel, recounted edge by edge:
+    each owner-path cover edge streams the streamer's other-level neighbours and its same-level
+    neighbours above v, and each owner's row is read once per work item."""
+    import math
+    spec = gen.rmat_spec(10, 16, 3)
+    s, d = spec.edges()
+    rp, col = oracle.build_csr(spec.n, s, d)
+    root = oracle.max_degree_root(rp)
+    lv = oracle.bfs_levels(rp, col, root)
+    ref = oracle.count(spec.n, s, d, root, want_cover=True)
+    assert np.array_equal(ref["level"], lv)
+    cu, cv = ref["cover_u"].astype(np.int64), ref["cover_v"].astype(np.int64)
+    deg = np.diff(rp.astype(np.int64))
+    nbrs = [col[rp[x]:rp[x + 1]].astype(np.int64) for x in range(spec.n)]
+    for smax, per_item in ((0, 3), (8, 512), (32, 7)):
+        hb = bench.hash_kernel_bytes(rp, col, lv, ref["cover_u"], ref["cover_v"],
+                                     {"small_max_degree": smax, "edges_per_item": per_item})
+        streamed = edges = 0
+        per_edge_bytes = 0
+        owner_edges = {}
+        for u, v in zip(cu.tolist(), cv.tolist()):
+            if deg[u] <= smax and deg[v] <= smax:
+                continue
+            h, x = (v, u) if (deg[v] > deg[u] or (deg[v] == deg[u] and v > u)) else (u, v)
+            vm = max(u, v)
+            nx = nbrs[x]
+            k = int(np.sum(lv[nx] != lv[x]) + np.sum((lv[nx] == lv[x]) & (nx > vm)))
+            streamed += k
+            edges += 1
+            per_edge_bytes += 4 * k + 32 + 4 * math.ceil(math.log2(max(int(deg[x]), 2)))
+            owner_edges[h] = owner_edges.get(h, 0) + 1
+        items = sum(-(-c // per_item) for c in owner_edges.values())
+        per_owner = sum(-(-c // per_item) * (4 * int(deg[h]) + 32) for h, c in owner_edges.items())
+        assert hb["streamed_elements"] == streamed and hb["edges"] == edges
+        assert hb["items"] == items and hb["bytes"] == per_edge_bytes + per_owner
